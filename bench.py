@@ -1,0 +1,314 @@
+"""Benchmark of the correlator stage on one B300.
+
+Default workload: the AARTFAAC-12-shaped array -- 576 dual-polarisation
+antennas (1152 inputs), 16 subbands of complex int16 samples (sigma 512, three
+point sources), 195,313 samples per subband per 1 s integration, a 16-tap x
+64-channel filter bank.  One step = one 1 s integration pushed through the
+whole stage: channeliser (FIR + FFT + bandpass + transpose, fp16 output) and
+the tcgen05 X-engine in FP16 mode.  The metric is useful X-engine tera-ops
+per second: 8 * N(N+1)/2 * spectra * channels * subbands per step.
+
+Also measured in the same run (reported as extra keys): the split-FP16 mode
+and the plain FP32 CUDA-core path on the same workload, the INT8-exact raw
+subband X-engine on the AARTFAAC-6-shaped array (576 inputs, 8 subbands), the
+channeliser's HBM throughput, an end-to-end pass through the C ABI with host
+buffers, and the fp64 CPU oracle on a bounded sample (cpu_baseline).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl acf|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "X-engine TOPS & frac of INT8/FP16 TC peak at 576 ants vs plain FP32 GPU path"
+UNIT = "TOPS"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"], src="measured")
+    return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
+
+
+def xops(N, T, n_ch, n_sb):
+    """Algorithmic X-engine ops: one complex MAC (8 real ops) per baseline per spectrum."""
+    return 8.0 * N * (N + 1) / 2 * T * n_ch * n_sb
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def cpu_oracle_sample(seconds_hint=True):
+    """fp64 oracle on a bounded slice of the default workload: subband 0, two
+    channels, all 1152 inputs, one 1 s integration (195,313 samples)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    w = synth.WORKLOADS["a12"]
+    N, S = w["n_inputs"], w["n_samples"]
+    sky = synth.make_sky(N, w["n_sources"], w["flux"], w["seed"])
+    x = synth.voltages(N, S, 1, "ci16", w["sigma"], sky, w["seed"], device="cpu")[0].numpy()
+    C, P = w["n_channels"], w["n_taps"]
+    chans = [0, 17]
+    t0 = time.perf_counter()
+    X = oracle.channelise(x, oracle.prototype(P, C), P, C, chans=chans)
+    V = oracle.correlate(X)
+    dt = time.perf_counter() - t0
+    T = X.shape[2]
+    ops = xops(N, T, len(chans), 1)
+    assert np.isfinite(V).all()
+    return dict(value=ops / dt / 1e12, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+                sample="A-12 workload, subband 0, channels {0, 17}, 1152 inputs, 1 s (3051 spectra); "
+                       "fp64 direct FIR + naive DFT + brute-force pairs, %.1f s" % dt, seconds=dt)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample())
+    v = statistics.median([r["value"] for r in vals])
+    secs = sum(r["seconds"] for r in vals)
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * secs / max(1, args.steps), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload="A-12: 1152 inputs x 16 subbands x 195313 ci16 samples, 64 ch x 16 taps; "
+                                     "oracle timed on subband 0, 2 channels"),
+                impl="reference", cpu_baseline=dict(vals[-1], value=v),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    line["cpu_baseline"].pop("seconds", None)
+    print(json.dumps(line))
+    return 0
+
+
+def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
+    """Steps of the whole stage in one precision mode; returns dict with timings."""
+    N, n_sb, C, P = w["n_inputs"], w["n_subbands"], w["n_channels"], w["n_taps"]
+    S = w["n_samples"]
+    c = acf.Correlator(N, n_sb, C, P, 1, mode, w["dtype"], S)
+    c.enable_timing(True)
+    out = c.empty_visibilities()
+    Ts, chan_ms, xeng_ms = [], [], []
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            c.push(x, stream)
+            c.visibilities(out, stream)
+        stream.synchronize()
+        l0 = acf.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        total_ms = 0.0
+        for _ in range(steps):
+            e0.record(stream)
+            c.push(x, stream)
+            c.visibilities(out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            Ts.append(c.query()["last_spectra"])
+            a, b = c.last_timing()
+            chan_ms.append(a)
+            xeng_ms.append(b)
+        launches = acf.launch_count() - l0
+    c.close()
+    ops = sum(xops(N, T, C, n_sb) for T in Ts)
+    return dict(ms_per_step=total_ms / steps, tops=ops / (total_ms * 1e-3) / 1e12, T=Ts,
+                chan_ms=statistics.median(chan_ms), xeng_ms=statistics.median(xeng_ms),
+                xeng_tops=xops(N, statistics.median(Ts), C, n_sb) / (statistics.median(xeng_ms) * 1e-3) / 1e12,
+                launches=launches, ops_per_step=ops / steps)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="acf", choices=["acf", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the comparison modes and the e2e pass")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_1609_04205_b300 as acf
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = peaks()
+    w = dict(synth.WORKLOADS["a12"])
+    N, n_sb, S = w["n_inputs"], w["n_subbands"], w["n_samples"]
+    sky = synth.make_sky(N, w["n_sources"], w["flux"], w["seed"] + rank)
+    x = synth.voltages(N, S, n_sb, w["dtype"], w["sigma"], sky, w["seed"] + rank, device=dev)
+    in_bytes = x.numel() * x.element_size()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+
+    # ---- headline: FP16 tensor-core mode, whole stage, inputs resident (14.4 GB > L2)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = Clocks(local)
+    main_r = time_mode(acf, torch, x, w, "fp16", args.steps, args.warmup, stream)
+    clocks = clk.stop()
+    ms = main_r["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = main_r["ops_per_step"] * world / (ms * 1e-3) / 1e12
+
+    extra = {}
+    if not args.quick:
+        r3 = time_mode(acf, torch, x, w, "fp16x3", max(2, args.steps // 2), 2, stream)
+        extra["fp16x3"] = dict(tops=r3["tops"], xeng_tops=r3["xeng_tops"], ms_per_step=r3["ms_per_step"],
+                               issued_tensor_tops=3 * r3["xeng_tops"])
+        r32 = time_mode(acf, torch, x, w, "fp32", 2, 1, stream)
+        extra["fp32_cuda_core"] = dict(tops=r32["tops"], xeng_tops=r32["xeng_tops"], ms_per_step=r32["ms_per_step"])
+        extra["fp16_speedup_vs_fp32_path"] = main_r["tops"] / r32["tops"]
+        extra["fp16x3_speedup_vs_fp32_path"] = r3["tops"] / r32["tops"]
+        # INT8-exact raw subbands, AARTFAAC-6 shape
+        w6 = dict(synth.WORKLOADS["a6"])
+        w6.update(n_channels=1, n_taps=1)
+        del x
+        torch.cuda.empty_cache()
+        x6 = synth.voltages(w6["n_inputs"], w6["n_samples"], w6["n_subbands"], "ci8", w6["sigma"], None, w6["seed"],
+                            device=dev)
+        r8 = time_mode(acf, torch, x6, w6, "int8", max(2, args.steps // 2), 2, stream)
+        extra["int8_raw_a6"] = dict(tops=r8["tops"], xeng_tops=r8["xeng_tops"], ms_per_step=r8["ms_per_step"],
+                                    workload="576 inputs x 8 subbands x 195313 ci8 samples, raw subband, exact")
+        del x6
+        torch.cuda.empty_cache()
+        x = synth.voltages(N, S, n_sb, w["dtype"], w["sigma"], sky, w["seed"] + rank, device=dev)
+
+    # channeliser HBM throughput (algorithmic bytes: ci16 in + fp16 out)
+    out_bytes = n_sb * w["n_channels"] * 2 * N * statistics.median(main_r["T"]) * 2
+    chan_gbs = (in_bytes + out_bytes) / (main_r["chan_ms"] * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.quick:
+        try:
+            xh = x.cpu().pin_memory()
+            c = acf.Correlator(N, n_sb, w["n_channels"], w["n_taps"], 1, "fp16", w["dtype"], S)
+            outh = torch.empty((n_sb, w["n_channels"], N * (N + 1) // 2, 2), dtype=torch.float32).pin_memory()
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    c.push(xh, stream)
+                    c.visibilities(outh, stream)
+                stream.synchronize()
+                k = max(2, args.steps // 2)
+                t0 = time.perf_counter()
+                ops = 0.0
+                for _ in range(k):
+                    c.push(xh, stream)
+                    c.visibilities(outh, stream)
+                    ops += xops(N, c.query()["last_spectra"], w["n_channels"], n_sb)
+                stream.synchronize()
+                dt = time.perf_counter() - t0
+            c.close()
+            e2e = dict(value=ops / dt / 1e12, unit=UNIT, h2d_bytes_per_step=in_bytes,
+                       d2h_bytes_per_step=outh.numel() * 4)
+            del xh, outh
+        except Exception as ex:  # pinned host memory may be short on some hosts
+            e2e = dict(value=None, unit=UNIT, h2d_bytes_per_step=in_bytes, d2h_bytes_per_step=0,
+                       note="e2e failed: %s" % ex)
+
+    cpu = None
+    if rank == 0 and not args.quick:
+        import oracle
+        oracle.build()
+        cpu = cpu_oracle_sample()
+        cpu.pop("seconds", None)
+
+    xeng_ms = main_r["xeng_ms"]
+    achieved = main_r["xeng_tops"]
+    roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16_sus"], unit="TFLOP/s",
+                frac=achieved / pk["bf16_sus"], traffic=None,
+                note="X-engine (k_xeng_tc, FP16 operands, fp32 accumulation); algorithmic ops "
+                     "8*N(N+1)/2*spectra*channels*subbands = %.3e per launch over its CUDA-event time %.3f ms; "
+                     "peak = %s bf16 sustained (fp16 dense = bf16 dense on B300); frac of burst %.3f"
+                     % (main_r["ops_per_step"], xeng_ms, pk["src"], achieved / pk["bf16"]))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="fp16",
+                data="synthetic",
+                config=dict(workload="A-12: 1152 inputs (576 dual-pol antennas) x 16 subbands x 195313 ci16 "
+                                     "samples (1 s), 64 ch x 16 taps, FP16 tensor-core X-engine",
+                            global_batch=n_sb * world, l2="inputs 14.4 GB > L2 (no flush needed)",
+                            parallelism="independent subband sets per rank" if world > 1 else "single GPU"),
+                roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
+                channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
+                                 bytes=in_bytes + out_bytes),
+                e2e=e2e, cpu_baseline=cpu, modes=extra)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -93,6 +93,15 @@ int oracle_channelise(const double *x, long S, int N, const double *h, int P, in
     if (m_end < m_begin) return -1;
     if (m_end > m_begin && (m_end - 1) * (long)C + (long)P * C > S) return -1;
     const long T = m_end - m_begin;
+    /* DFT kernel exp(-2 pi i c q / C) for the selected channels, evaluated once */
+    double *wr = (double *)malloc(sizeof(double) * (size_t)n_chans * C);
+    double *wi = (double *)malloc(sizeof(double) * (size_t)n_chans * C);
+    for (int ci = 0; ci < n_chans; ++ci)
+        for (int q = 0; q < C; ++q) {
+            const double ang = -2.0 * ORACLE_PI * (double)(((long)chans[ci] * q) % C) / (double)C;
+            wr[(size_t)ci * C + q] = cos(ang);
+            wi[(size_t)ci * C + q] = sin(ang);
+        }
 #pragma omp parallel
     {
         double *y = (double *)malloc(sizeof(double) * 2 * (size_t)C);
@@ -116,8 +125,7 @@ int oracle_channelise(const double *x, long S, int N, const double *h, int P, in
                     const int c = chans[ci];
                     double re = 0.0, im = 0.0;
                     for (int q = 0; q < C; ++q) {
-                        const double ang = -2.0 * ORACLE_PI * (double)(((long)c * q) % C) / (double)C;
-                        const double cr = cos(ang), sr = sin(ang);
+                        const double cr = wr[(size_t)ci * C + q], sr = wi[(size_t)ci * C + q];
                         re += y[2 * q] * cr - y[2 * q + 1] * sr;
                         im += y[2 * q] * sr + y[2 * q + 1] * cr;
                     }
@@ -130,6 +138,8 @@ int oracle_channelise(const double *x, long S, int N, const double *h, int P, in
         }
         free(y);
     }
+    free(wr);
+    free(wi);
     return 0;
 }
 

@@ -1,0 +1,80 @@
+// Internal declarations shared by the libacf translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <atomic>
+#include <string>
+
+#include "acf.h"
+
+namespace acf {
+
+// Host-side count of kernel launches (graph replays add their node count).
+extern std::atomic<long long> g_launches;
+
+// Device-side error word written by bounded waits (0 = fine).  One per
+// device, allocated on first use by the runtime.
+int *device_error_word();
+
+enum OutKind { OUT_F32 = 0, OUT_F16 = 1, OUT_F16X3 = 2 };
+
+inline int in_elem_bytes(acf_in_dtype d) { return d == ACF_IN_CI8 ? 2 : d == ACF_IN_CI16 ? 4 : 8; }
+inline long round_up(long a, long b) { return (a + b - 1) / b * b; }
+inline long n_baselines(long n) { return n * (n + 1) / 2; }
+
+// ---- channeliser (chan_ppf.cu) -------------------------------------------
+// Twiddle table exp(-2 pi i k / C), k < C, float2, device.
+cudaError_t make_twiddles(int C, float2 **d_tw);
+cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples, long n_samples,
+                              acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
+                              const float *bandpass, const float2 *tw, int out_kind, void *out,
+                              void *out_lo, long t_stride, float scale, long T,
+                              cudaStream_t s);
+cudaError_t launch_transpose_raw(const void *samples, long n_samples, acf_in_dtype dt, int n_sb,
+                                 int N, int out_kind, void *out, void *out_lo, long t_stride,
+                                 float scale, cudaStream_t s);
+// Copy stream samples [from, from + count) of (hist ++ samples) into dst
+// ([n_sb][count][N]); used to carry the filter-bank history across pushes.
+cudaError_t launch_history(const void *hist, long n_hist, const void *samples, long n_samples,
+                           acf_in_dtype dt, int n_sb, int N, long from, long count, void *dst,
+                           long dst_cap, cudaStream_t s);
+
+// ---- X-engines --------------------------------------------------------------
+cudaError_t launch_xeng_simt(const float *x, int n_problems, int N, long n_time, long t_stride,
+                             float vscale, float2 *V, cudaStream_t s);
+
+// One job of the tensor-core X-engine work list.
+struct TcJob {
+    const __half *x;      // operand (hi), [n_problems][2N][t_stride]
+    const __half *x_lo;   // lo part (FP16x3) or nullptr
+    void *V;              // accumulator, [n_problems][NB] complex float or int64
+    int N;                // complex inputs
+    int n_problems;       // subbands * channels
+    long n_time;          // valid spectra (K extent; zero padded to 64)
+    long t_stride;        // row stride in elements
+    int mode;             // ACF_X_FP16, ACF_X_FP16x3 or ACF_X_INT8
+    float vscale;
+};
+struct TcPlan;            // opaque: tensor maps + work list on the device
+struct TcTuning {
+    int n_tile = 256;     // real rows per N tile: 128 or 256
+    int k_split = 1;      // time split factor per tile (atomically reduced)
+    int order = 0;        // 0: problem-major, 1: longest-first
+};
+cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, TcPlan **out,
+                           std::string *err);
+cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s);
+// Per-launch job parameters: valid spectra and the fp result scale.
+cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale);
+int tc_plan_items(const TcPlan *p);
+void tc_plan_destroy(TcPlan *p);
+bool tc_supported(int device);
+
+// ---- gain (gain.cu) ---------------------------------------------------------
+cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N, int C,
+                        float *loss, float2 *grad, float *partials, int n_partials_cap,
+                        cudaStream_t s);
+int gain_partials_needed(int N, int C);
+
+}  // namespace acf

@@ -1,0 +1,337 @@
+// Ragged batch: many independent arrays (different input and channel counts)
+// correlated by one persistent tensor-core X-engine launch, with every step
+// captured in a single CUDA graph (the paper spreads independent subbands
+// over free GPUs, Sec. 4.2 "GPU processing"; on one B300 the independent
+// problems share one persistent launch instead).
+//
+// Raw jobs (n_channels == 1) run INT8-exact; channelised jobs run the split
+// fp16 path after the filter bank.  The autotuner times the X-engine launch
+// for each candidate (N tile 128/256, time split 1/2/4, job order) on the
+// real geometry and keeps the fastest.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "acf_internal.h"
+
+namespace acf {
+namespace {
+thread_local std::string g_batch_create_err;
+
+long spectra_of(long len, int P, int C)
+{
+    const long L = (long)P * C;
+    return len < L ? 0 : (len - L) / C + 1;
+}
+
+void proto(int P, int C, std::vector<float> &h)
+{
+    const long L = (long)P * C;
+    h.assign(L, 0.f);
+    if (L == 1) {
+        h[0] = 1.f;
+        return;
+    }
+    std::vector<double> d(L);
+    double sum = 0;
+    for (long n = 0; n < L; ++n) {
+        const double w = 0.5 - 0.5 * std::cos(2.0 * M_PI * (double)n / (double)(L - 1));
+        const double u = ((double)n - 0.5 * (double)(L - 1)) / (double)C;
+        const double s = (u == 0.0) ? 1.0 : std::sin(M_PI * u) / (M_PI * u);
+        d[n] = w * s;
+        sum += d[n];
+    }
+    for (long n = 0; n < L; ++n) h[n] = (float)(d[n] / sum);
+}
+}  // namespace
+}  // namespace acf
+
+using namespace acf;
+
+struct acf_batch {
+    std::vector<acf_job> jobs;
+    std::vector<long> T, t_stride;
+    std::vector<void *> X, Xlo;
+    std::vector<size_t> v_bytes;
+    std::vector<float> scale;
+    std::map<long, float *> d_h;        // key P*1024 + C
+    std::map<int, float2 *> d_tw;       // key C
+    std::map<int, float *> d_bp;        // key C (all ones)
+    TcTuning tun;
+    TcPlan *plan = nullptr;
+    cudaStream_t s_int = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void *> g_in;
+    std::vector<void *> g_out;
+    long long graph_kernels = 0;
+    std::string err;
+};
+
+static acf_status bf(acf_batch *b, acf_status s, const std::string &m)
+{
+    if (b) b->err = m;
+    else g_batch_create_err = m;
+    return s;
+}
+
+static std::vector<TcJob> tc_jobs(const acf_batch *b, void *const *outputs)
+{
+    std::vector<TcJob> v(b->jobs.size());
+    for (size_t k = 0; k < b->jobs.size(); ++k) {
+        TcJob &j = v[k];
+        const bool raw = b->jobs[k].n_channels == 1;
+        j.x = static_cast<const __half *>(b->X[k]);
+        j.x_lo = static_cast<const __half *>(b->Xlo[k]);
+        j.V = outputs[k];
+        j.N = b->jobs[k].n_inputs;
+        j.n_problems = b->jobs[k].n_channels;
+        j.n_time = b->T[k];
+        j.t_stride = b->t_stride[k];
+        j.mode = raw ? ACF_X_INT8 : ACF_X_FP16x3;
+        j.vscale = raw ? 1.f : 1.f / (b->scale[k] * b->scale[k]);
+    }
+    return v;
+}
+
+// Enqueue the whole batch (no graph) on stream s.
+static cudaError_t enqueue_all(acf_batch *b, const void *const *inputs, void *const *outputs, cudaStream_t s)
+{
+    cudaError_t e;
+    for (size_t k = 0; k < b->jobs.size(); ++k) {
+        const acf_job &J = b->jobs[k];
+        if ((e = cudaMemsetAsync(outputs[k], 0, b->v_bytes[k], s)) != cudaSuccess) return e;
+        if (b->T[k] == 0) continue;
+        if (J.n_channels == 1) {
+            e = launch_transpose_raw(inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, OUT_F16, b->X[k], nullptr,
+                                     b->t_stride[k], 1.f, s);
+        } else {
+            e = launch_channelise(nullptr, 0, inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, J.n_channels, J.n_taps,
+                                  b->d_h[(long)J.n_taps * 1024 + J.n_channels], b->d_bp[J.n_channels],
+                                  b->d_tw[J.n_channels], OUT_F16X3, b->X[k], b->Xlo[k], b->t_stride[k], b->scale[k],
+                                  b->T[k], s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return tc_plan_launch(b->plan, s);
+}
+
+static cudaError_t rebuild_plan(acf_batch *b, void *const *outputs, const TcTuning &tun)
+{
+    if (b->plan) {
+        tc_plan_destroy(b->plan);
+        b->plan = nullptr;
+    }
+    std::vector<TcJob> js = tc_jobs(b, outputs);
+    std::string perr;
+    cudaError_t e = tc_plan_create(js.data(), (int)js.size(), tun, &b->plan, &perr);
+    if (e != cudaSuccess) b->err = "tensor-core plan: " + perr;
+    return e;
+}
+
+static void autotune(acf_batch *b)
+{
+    // scratch outputs for timing
+    std::vector<void *> outs(b->jobs.size(), nullptr);
+    for (size_t k = 0; k < outs.size(); ++k)
+        if (cudaMalloc(&outs[k], b->v_bytes[k]) != cudaSuccess) {
+            for (void *p : outs) cudaFree(p);
+            cudaGetLastError();
+            return;
+        }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    TcTuning best_t = b->tun;
+    for (int nt : {256, 128})
+        for (int ks : {1, 2, 4})
+            for (int order : {1, 0}) {
+                TcTuning t;
+                t.n_tile = nt;
+                t.k_split = ks;
+                t.order = order;
+                if (rebuild_plan(b, outs.data(), t) != cudaSuccess) continue;
+                tc_plan_launch(b->plan, b->s_int);   // warm-up
+                cudaEventRecord(e0, b->s_int);
+                for (int r = 0; r < 3; ++r) tc_plan_launch(b->plan, b->s_int);
+                cudaEventRecord(e1, b->s_int);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_t = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tun = best_t;
+    for (void *p : outs) cudaFree(p);
+    if (b->plan) {
+        tc_plan_destroy(b->plan);
+        b->plan = nullptr;
+    }
+}
+
+extern "C" {
+
+acf_status acf_batch_create(acf_batch **out, const acf_job *jobs, int n_jobs, int tune)
+{
+    if (!out) return bf(nullptr, ACF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n_jobs < 1 || n_jobs > 64) return bf(nullptr, ACF_EINVAL, "need 1..64 jobs");
+    for (int k = 0; k < n_jobs; ++k) {
+        const acf_job &J = jobs[k];
+        const bool cok = J.n_channels == 1 || J.n_channels == 16 || J.n_channels == 64 || J.n_channels == 256;
+        if (J.n_inputs < 1 || J.n_inputs > 65536 || !cok || J.n_taps < 1 || J.n_taps > 32 ||
+            (J.n_channels == 1 && J.n_taps != 1) || J.n_samples < 1 || J.n_samples > (1L << 30))
+            return bf(nullptr, ACF_EINVAL, "job " + std::to_string(k) + ": bad geometry");
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bf(nullptr, ACF_ECUDA, "cudaGetDevice failed");
+    if (!tc_supported(dev)) return bf(nullptr, ACF_EUNSUPPORTED, "the batch runs on sm_103 tensor cores");
+    acf_batch *b = new acf_batch();
+    b->jobs.assign(jobs, jobs + n_jobs);
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&](acf_status s, const std::string &m) {
+        acf_batch_destroy(b);
+        return bf(nullptr, s, m);
+    };
+    for (int k = 0; k < n_jobs; ++k) {
+        const acf_job &J = jobs[k];
+        const bool raw = J.n_channels == 1;
+        const long T = raw ? J.n_samples : spectra_of(J.n_samples, J.n_taps, J.n_channels);
+        const long ts = round_up(std::max<long>(T, 1), 64);
+        const size_t xb = (size_t)J.n_channels * 2 * J.n_inputs * ts * 2;
+        void *x = nullptr, *xl = nullptr;
+        if ((e = cudaMalloc(&x, xb)) != cudaSuccess) return cleanup(ACF_ENOMEM, "operand alloc");
+        b->X.push_back(x);
+        if (!raw) {
+            if ((e = cudaMalloc(&xl, xb)) != cudaSuccess) return cleanup(ACF_ENOMEM, "operand alloc");
+        }
+        b->Xlo.push_back(xl);
+        cudaMemset(x, 0, xb);
+        if (xl) cudaMemset(xl, 0, xb);
+        b->T.push_back(T);
+        b->t_stride.push_back(ts);
+        b->v_bytes.push_back((size_t)J.n_channels * n_baselines(J.n_inputs) * (raw ? 16 : 8));
+        float sc = 1.f;
+        if (!raw) {
+            const long key = (long)J.n_taps * 1024 + J.n_channels;
+            std::vector<float> h;
+            proto(J.n_taps, J.n_channels, h);
+            if (!b->d_h.count(key)) {
+                float *d = nullptr;
+                if ((e = cudaMalloc(&d, sizeof(float) * h.size())) != cudaSuccess) return cleanup(ACF_ENOMEM, "alloc");
+                cudaMemcpy(d, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice);
+                b->d_h[key] = d;
+            }
+            if (!b->d_tw.count(J.n_channels)) {
+                float2 *tw = nullptr;
+                if ((e = make_twiddles(J.n_channels, &tw)) != cudaSuccess) return cleanup(ACF_ENOMEM, "alloc");
+                b->d_tw[J.n_channels] = tw;
+                std::vector<float> ones(J.n_channels, 1.f);
+                float *d = nullptr;
+                if ((e = cudaMalloc(&d, sizeof(float) * J.n_channels)) != cudaSuccess) return cleanup(ACF_ENOMEM, "alloc");
+                cudaMemcpy(d, ones.data(), sizeof(float) * J.n_channels, cudaMemcpyHostToDevice);
+                b->d_bp[J.n_channels] = d;
+            }
+            double sabs = 0;
+            for (float v : h) sabs += std::fabs((double)v);
+            sc = std::ldexp(1.f, (int)std::floor(std::log2(60000.0 / (2.0 * sabs * 128.0))));
+        }
+        b->scale.push_back(sc);
+    }
+    if (!device_error_word()) return cleanup(ACF_ENOMEM, "device error word");
+    if ((e = cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking)) != cudaSuccess) return cleanup(ACF_ECUDA, "stream");
+    cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (tune) autotune(b);
+    if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(ACF_ECUDA, "device error during planning");
+    *out = b;
+    return ACF_OK;
+}
+
+acf_status acf_batch_run(acf_batch *b, const void *const *inputs, void *const *outputs, acf_stream_t stream)
+{
+    if (!b) return ACF_EINVAL;
+    if (!inputs || !outputs) return bf(b, ACF_EINVAL, "inputs / outputs is NULL");
+    const size_t n = b->jobs.size();
+    for (size_t k = 0; k < n; ++k)
+        if (!inputs[k] || !outputs[k]) return bf(b, ACF_EINVAL, "NULL input or output for job " + std::to_string(k));
+    cudaError_t e;
+    const bool same = b->gexec && std::equal(b->g_in.begin(), b->g_in.end(), inputs) &&
+                      std::equal(b->g_out.begin(), b->g_out.end(), outputs);
+    if (!same) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        if ((e = rebuild_plan(b, outputs, b->tun)) != cudaSuccess) return bf(b, ACF_ECUDA, b->err);
+        cudaGraph_t g = nullptr;
+        const long long before = g_launches.load();
+        if ((e = cudaStreamBeginCapture(b->s_int, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bf(b, ACF_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        cudaError_t eq = enqueue_all(b, inputs, outputs, b->s_int);
+        e = cudaStreamEndCapture(b->s_int, &g);
+        b->graph_kernels = g_launches.load() - before;
+        g_launches -= b->graph_kernels;   // captured, not launched
+        if (eq != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return bf(b, ACF_ECUDA, std::string("capture: ") + cudaGetErrorString(eq != cudaSuccess ? eq : e));
+        }
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bf(b, ACF_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        b->g_in.assign(inputs, inputs + n);
+        b->g_out.assign(outputs, outputs + n);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEventRecord(b->ev_in, s);
+    cudaStreamWaitEvent(b->s_int, b->ev_in, 0);
+    if ((e = cudaGraphLaunch(b->gexec, b->s_int)) != cudaSuccess)
+        return bf(b, ACF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    g_launches += b->graph_kernels;
+    cudaEventRecord(b->ev_out, b->s_int);
+    cudaStreamWaitEvent(s, b->ev_out, 0);
+    return ACF_OK;
+}
+
+acf_status acf_batch_query(const acf_batch *b, int *n_tile, int *k_split, int *n_items)
+{
+    if (!b) return ACF_EINVAL;
+    if (n_tile) *n_tile = b->tun.n_tile;
+    if (k_split) *k_split = b->tun.k_split;
+    if (n_items) *n_items = b->plan ? tc_plan_items(b->plan) : 0;
+    return ACF_OK;
+}
+
+acf_status acf_batch_destroy(acf_batch *b)
+{
+    if (!b) return ACF_OK;
+    cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->plan) tc_plan_destroy(b->plan);
+    for (void *p : b->X) cudaFree(p);
+    for (void *p : b->Xlo) cudaFree(p);
+    for (auto &kv : b->d_h) cudaFree(kv.second);
+    for (auto &kv : b->d_tw) cudaFree(kv.second);
+    for (auto &kv : b->d_bp) cudaFree(kv.second);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->s_int) cudaStreamDestroy(b->s_int);
+    delete b;
+    cudaGetLastError();
+    return ACF_OK;
+}
+
+const char *acf_batch_last_error(const acf_batch *b) { return b ? b->err.c_str() : g_batch_create_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Gain-corrupted correlation M = G R G^H, its squared-Frobenius loss against
+// observed visibilities and the adjoint (gradient) with respect to the
+// per-input complex gains -- the calibration-facing form of the correlator
+// output (Sec. 5 fits per-dipole gains to the visibilities).
+//
+// One pass over the packed lower triangles of R and V: a block owns a 64x64
+// tile of one channel's triangle, forms E = g_i R_ij conj(g_j) - V_ij per
+// element, adds w|E|^2 (w = 2 off the diagonal: the upper triangle is the
+// conjugate) to a per-block partial, and accumulates the gradient rows
+//   grad_i += 4 E_ij conj(R_ij) g_j      and, for i != j,
+//   grad_j += 4 conj(E_ij) R_ij g_i      (= 4 E_ji conj(R_ji) g_i).
+// Row sums are warp-reduced, column sums go through shared-memory atomics,
+// and one global atomic per (tile row/column) lands in grad.  The per-block
+// loss partials are summed by a second, single-block kernel in a fixed order,
+// so the loss is deterministic.
+#include "acf_internal.h"
+
+namespace acf {
+namespace {
+
+constexpr int GT = 64;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+__device__ __forceinline__ void tri_decode_g(int k, int &bi, int &bj) {
+    int b = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
+    while ((b + 1) * (b + 2) / 2 <= k) ++b;
+    while (b * (b + 1) / 2 > k) --b;
+    bi = b;
+    bj = k - b * (b + 1) / 2;
+}
+
+__global__ void __launch_bounds__(256)
+k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 *__restrict__ g,
+       int N, float *__restrict__ partials, float2 *__restrict__ grad)
+{
+    __shared__ float2 colacc[GT];
+    __shared__ float2 gi_s[GT], gj_s[GT];
+    __shared__ float red[8];
+    int bi, bj;
+    tri_decode_g(blockIdx.x, bi, bj);
+    const int c = blockIdx.y;
+    const int i0 = bi * GT, j0 = bj * GT;
+    const long NB = (long)N * (N + 1) / 2;
+    const float2 *Rc = R + (long)c * NB;
+    const float2 *Vc = V + (long)c * NB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < GT) {
+        colacc[tid] = make_float2(0.f, 0.f);
+        gi_s[tid] = (i0 + tid < N) ? g[i0 + tid] : make_float2(0.f, 0.f);
+        gj_s[tid] = (j0 + tid < N) ? g[j0 + tid] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float loss = 0.f;
+    // each warp walks rows; lane covers columns jj = lane and lane + 32
+    for (int ii = warp; ii < GT; ii += 8) {
+        const int i = i0 + ii;
+        float2 rowsum = make_float2(0.f, 0.f);
+        if (i < N) {
+            const long base = (long)i * (i + 1) / 2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jj = lane + 32 * h;
+                const int j = j0 + jj;
+                if (j <= i && j < N) {
+                    const float2 r = Rc[base + j], v = Vc[base + j];
+                    const float2 gi = gi_s[ii], gj = gj_s[jj];
+                    const float2 m = cmulf(cmulf(gi, r), conjf2(gj));
+                    const float2 e = make_float2(m.x - v.x, m.y - v.y);
+                    const float w = (i == j) ? 1.f : 2.f;
+                    loss = fmaf(w, e.x * e.x + e.y * e.y, loss);
+                    if (grad) {
+                        const float2 t = cmulf(cmulf(e, conjf2(r)), gj);
+                        rowsum.x += t.x;
+                        rowsum.y += t.y;
+                        if (i != j) {
+                            const float2 u = cmulf(cmulf(conjf2(e), r), gi);
+                            atomicAdd(&colacc[jj].x, u.x);
+                            atomicAdd(&colacc[jj].y, u.y);
+                        }
+                    }
+                }
+            }
+        }
+        if (grad) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                rowsum.x += __shfl_xor_sync(0xffffffffu, rowsum.x, o);
+                rowsum.y += __shfl_xor_sync(0xffffffffu, rowsum.y, o);
+            }
+            if (lane == 0 && i < N) atomicAdd(&grad[i], make_float2(4.f * rowsum.x, 4.f * rowsum.y));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane == 0) red[warp] = loss;
+    __syncthreads();
+    if (tid == 0) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        partials[(long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+    if (grad && tid < GT && j0 + tid < N) {
+        const float2 v = colacc[tid];
+        if (v.x != 0.f || v.y != 0.f) atomicAdd(&grad[j0 + tid], make_float2(4.f * v.x, 4.f * v.y));
+    }
+}
+
+// Fixed-order pairwise reduction of the partials into *loss.
+__global__ void __launch_bounds__(1024) k_reduce(const float *__restrict__ part, int n, float *loss)
+{
+    __shared__ float s[1024];
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < n; k += 1024) acc += part[k];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 512; w >= 1; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s[0];
+}
+
+}  // namespace
+
+int gain_partials_needed(int N, int C)
+{
+    const int nt = (N + GT - 1) / GT;
+    return nt * (nt + 1) / 2 * C;
+}
+
+cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N, int C,
+                        float *loss, float2 *grad, float *partials, int n_partials_cap,
+                        cudaStream_t s)
+{
+    const int nt = (N + GT - 1) / GT;
+    const int tiles = nt * (nt + 1) / 2;
+    if (tiles * C > n_partials_cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (grad) {
+        e = cudaMemsetAsync(grad, 0, sizeof(float2) * N, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_gain<<<dim3(tiles, C), 256, 0, s>>>(R, V, g, N, partials, grad);
+    g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (loss) {
+        k_reduce<<<1, 1024, 0, s>>>(partials, tiles * C, loss);
+        g_launches++;
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace acf

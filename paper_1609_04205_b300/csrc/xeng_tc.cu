@@ -1,0 +1,559 @@
+// Tensor-core X-engine for sm_103a (Sec. 4.2.5 on 5th-generation tensor cores).
+//
+// The complex rank-k update V = sum_t x_t x_t^H is computed as one REAL
+// product D = Y Y^T, where Y holds each complex input as two real rows
+// (2n = Re x_n, 2n+1 = Im x_n) with time along the row.  Every 2x2 block of D
+// gives one visibility:
+//     Re V_ij = D[2i][2j] + D[2i+1][2j+1],   Im V_ij = D[2i+1][2j] - D[2i][2j+1].
+// No negated or swapped operand copy is needed and the work equals the
+// complex product's 4 real MACs per baseline and sample.  Only tiles that
+// touch the lower triangle (i >= j) are computed; the epilogue masks the rest.
+//
+// Kernel structure (one persistent CTA per SM, 10 warps):
+//   warp 0     TMA producer: 64-sample K steps of a 128-row A tile and an
+//              NT-row B tile (SW128, K-major) into a ring of four 48 KB slots;
+//   warp 1     owns the TMEM allocation (2 x 256 fp32 columns = two
+//              accumulators) and one lane issues tcgen05.mma (M=128, N=NT,
+//              K=16, fp16 x fp16 -> fp32), committing each slot back to the
+//              producer and each finished chunk to the epilogue;
+//   warps 2-9  epilogue: tcgen05.ld the finished accumulator chunk, fold it
+//              into per-thread register masters (fp32, or int32 for the exact
+//              mode), and at the end of a work item combine the 2x2 blocks
+//              and atomically add the visibilities into the packed triangle.
+// Modes: FP16 (one product per K step), FP16x3 (hi*hi + hi*lo + lo*hi, the
+// lo operands in a second slot), INT8 (fp16 holding integers |x| <= 127:
+// products are exact and each 512-sample chunk sum stays below 2^24, so the
+// fp32 tensor-core accumulation is exact; chunks are folded into int32
+// masters and work items never exceed 65,536 samples, so the masters cannot
+// overflow; the final combine is in int64).
+// Every mbarrier wait is bounded; on timeout the CTA records an error word,
+// drains its own TMA copies and MMAs, frees TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "acf_internal.h"
+
+namespace acf {
+namespace {
+
+constexpr int kMaxJobs = 64;
+constexpr int kSlots = 4;
+constexpr int kSlotBytes = 48 * 1024;          // A 16 KB + B up to 32 KB
+constexpr int kBM = 128, kBK = 64;
+constexpr int kThreadsTc = 320;
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitLimit = 1LL << 22;   // x 256 ns back-off: about one second
+
+struct JobDev {
+    void *V;
+    int N, n_problems, mode, nt;
+    long n_time;
+    int k_split, tiles_pp, mb, item_begin;
+    float vscale;
+};
+
+struct TcParams {
+    CUtensorMap maps[kMaxJobs][2];
+    JobDev jobs[kMaxJobs];
+    int n_jobs;
+    int n_items;
+    int *err;
+};
+
+struct Item {
+    int job, p, bi, bj;
+    long k0, k1;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false on abort/timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err, int code) {
+    for (long long it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it >= 64) {
+            if (*abort_flag) return false;
+            __nanosleep(256);
+            if (it > kWaitLimit) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+    d |= (uint64_t)(16u >> 4) << 16;                  // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                // SBO: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ uint32_t idesc_f16(int nt) {
+    // D fp32, A/B fp16, both K-major, N = nt, M = 128
+    return (1u << 4) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Lower-triangle tiles of one problem, bj-major: tile count and decode.
+__host__ __device__ __forceinline__ int bi_min(int bj, int nt) {
+    const int v = (nt / 2) * bj - 63;
+    return v <= 0 ? 0 : (v + 63) / 64;
+}
+__host__ __device__ inline int tiles_per_problem(int N, int nt) {
+    const int mb = (2 * N + kBM - 1) / kBM;
+    const int nb = (2 * N + nt - 1) / nt;
+    int t = 0;
+    for (int bj = 0; bj < nb; ++bj) t += max(0, mb - bi_min(bj, nt));
+    return t;
+}
+
+__device__ __forceinline__ bool decode_item(const TcParams &P, int item, Item &it) {
+    int j = 0;
+    while (j + 1 < P.n_jobs && item >= P.jobs[j + 1].item_begin) ++j;
+    const JobDev &J = P.jobs[j];
+    int local = item - J.item_begin;
+    const int per_p = J.tiles_pp * J.k_split;
+    it.job = j;
+    it.p = local / per_p;
+    int rem = local - it.p * per_p;
+    int tile = rem / J.k_split;
+    const int s = rem - tile * J.k_split;
+    int bj = 0;
+    for (;; ++bj) {
+        const int cnt = J.mb - bi_min(bj, J.nt);
+        if (tile < cnt) break;
+        tile -= cnt;
+    }
+    it.bj = bj;
+    it.bi = bi_min(bj, J.nt) + tile;
+    const long K64 = (J.n_time + 63) / 64 * 64;
+    const long per = ((K64 + J.k_split - 1) / J.k_split + 63) / 64 * 64;
+    it.k0 = (long)s * per;
+    it.k1 = min(K64, it.k0 + per);
+    return it.k0 < it.k1;
+}
+
+__device__ __forceinline__ int chunk_steps(int mode) {
+    return mode == ACF_X_INT8 ? 8 : (mode == ACF_X_FP16x3 ? 16 : (1 << 30));
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant__ TcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the SW128 tiles
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            for (int j = 0; j < P.n_jobs; ++j) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.maps[j][0])) : "memory");
+            }
+            long pos = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                Item it;
+                if (!decode_item(P, item, it)) continue;
+                const JobDev &J = P.jobs[it.job];
+                const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
+                const int rowA = it.p * 2 * J.N + it.bi * kBM;
+                const int rowB = it.p * 2 * J.N + it.bj * J.nt;
+                const uint32_t bytes = (uint32_t)(kBM + J.nt) * kBK * 2;
+                for (long k = it.k0; k < it.k1 && ok; k += kBK) {
+                    for (int h = 0; h < spk && ok; ++h) {
+                        const int slot = (int)(pos % kSlots);
+                        const uint32_t ph = (uint32_t)((pos / kSlots) & 1);
+                        ok = mbar_wait(smem_u32(&empty_bar[slot]), ph ^ 1, &abort_flag, P.err, 1);
+                        if (!ok) break;
+                        const uint32_t fb = smem_u32(&full_bar[slot]);
+                        mbar_expect_tx(fb, bytes);
+                        const uint32_t base = smem_u32(smem + slot * kSlotBytes);
+                        const CUtensorMap *map = &P.maps[it.job][h];
+                        tma_load_2d(base, map, fb, (int)k, rowA);
+                        for (int q = 0; q < J.nt / kBM; ++q)
+                            tma_load_2d(base + (kBM + q * kBM) * kBK * 2, map, fb, (int)k, rowB + q * kBM);
+                        ++pos;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain our own copies still in flight before the CTA exits
+                for (long q = pos - 1; q >= 0 && q >= pos - kSlots; --q) {
+                    const int slot = (int)(q % kSlots);
+                    for (long long it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&full_bar[slot]), (uint32_t)((q / kSlots) & 1)); ++it)
+                        __nanosleep(256);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            long pos = 0, cc = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                Item it;
+                if (!decode_item(P, item, it)) continue;
+                const JobDev &J = P.jobs[it.job];
+                const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
+                const uint32_t idesc = idesc_f16(J.nt);
+                const long steps = (it.k1 - it.k0) / kBK;
+                const long csteps = chunk_steps(J.mode);
+                for (long s0 = 0; s0 < steps && ok; s0 += csteps) {
+                    const int b = (int)(cc & 1);
+                    ok = mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((cc >> 1) & 1) ^ 1), &abort_flag, P.err, 2);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t dt = tmem + (uint32_t)(b * 256);
+                    const long s1 = min(steps, s0 + csteps);
+                    for (long s = s0; s < s1 && ok; ++s) {
+                        int slot[2];
+                        for (int h = 0; h < spk; ++h) {
+                            slot[h] = (int)(pos % kSlots);
+                            const uint32_t ph = (uint32_t)((pos / kSlots) & 1);
+                            ok = ok && mbar_wait(smem_u32(&full_bar[slot[h]]), ph, &abort_flag, P.err, 3);
+                            ++pos;
+                        }
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a_hi = smem_u32(smem + slot[0] * kSlotBytes);
+                        const uint32_t b_hi = a_hi + kBM * kBK * 2;
+                        const uint64_t dah = desc_sw128(a_hi), dbh = desc_sw128(b_hi);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint32_t acc = (s > s0 || kk > 0) ? 1u : 0u;
+                            mma_f16(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
+                            if (spk == 2) {
+                                const uint32_t a_lo = smem_u32(smem + slot[1] * kSlotBytes);
+                                const uint32_t b_lo = a_lo + kBM * kBK * 2;
+                                const uint64_t dal = desc_sw128(a_lo), dbl = desc_sw128(b_lo);
+                                mma_f16(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
+                                mma_f16(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
+                            }
+                        }
+                        for (int h = 0; h < spk; ++h) mma_commit(smem_u32(&empty_bar[slot[h]]));
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(&accf_bar[b]));
+                    ++cc;
+                }
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            mma_commit(smem_u32(&done_bar));
+            for (long long it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&done_bar), 0); ++it) __nanosleep(256);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        const int q = warp & 3;                 // TMEM lane quadrant
+        const int half = (warp - 2) >> 2;       // column half
+        const int odd = lane & 1;
+        uint32_t m[128];
+#pragma unroll
+        for (int k = 0; k < 128; ++k) m[k] = 0u;
+        long cc = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            Item it;
+            if (!decode_item(P, item, it)) continue;
+            const JobDev &J = P.jobs[it.job];
+            const bool exact = J.mode == ACF_X_INT8;
+            const bool active = half * 128 < J.nt;
+            const long steps = (it.k1 - it.k0) / kBK;
+            const long csteps = chunk_steps(J.mode);
+            for (long s0 = 0; s0 < steps; s0 += csteps) {
+                const int b = (int)(cc & 1);
+                // one lane waits; the warp follows its verdict (keeps .sync.aligned loads converged)
+                int w_ok = 0;
+                if (lane == 0) w_ok = mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((cc >> 1) & 1), &abort_flag, P.err, 4);
+                ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+                if (!ok) break;
+                tc_fence_after();
+                if (active) {
+                    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 256 + half * 128);
+#pragma unroll
+                    for (int piece = 0; piece < 4; ++piece) {
+                        uint32_t r[32];
+                        tmem_ld32(tbase + piece * 32, r);
+                        tmem_wait_ld();
+                        if (exact) {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k)
+                                m[piece * 32 + k] = (uint32_t)((int)m[piece * 32 + k] + __float2int_rn(__uint_as_float(r[k])));
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k)
+                                m[piece * 32 + k] = __float_as_uint(__uint_as_float(m[piece * 32 + k]) + __uint_as_float(r[k]));
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
+                ++cc;
+            }
+            if (!ok) break;
+            if (!active) continue;
+            // flush: combine 2x2 real blocks into complex visibilities
+            const int i = it.bi * 64 + 16 * q + (lane >> 1);
+            const int jbase = (J.nt * it.bj + 128 * half) / 2 + 32 * odd;
+            const long NB = (long)J.N * (J.N + 1) / 2;
+            const long prow = (long)it.p * NB + (long)i * (i + 1) / 2;
+            const bool row_ok = i < J.N;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const uint32_t s0v = odd ? m[2 * k] : m[64 + 2 * k];
+                const uint32_t s1v = odd ? m[2 * k + 1] : m[65 + 2 * k];
+                const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0v, 1);
+                const uint32_t r1 = __shfl_xor_sync(0xffffffffu, s1v, 1);
+                const uint32_t own0 = odd ? m[64 + 2 * k] : m[2 * k];
+                const uint32_t own1 = odd ? m[65 + 2 * k] : m[2 * k + 1];
+                // even lane: a = own0, b = own1, c = r0, d = r1
+                // odd lane:  c = own0, d = own1, a = r0, b = r1
+                const int j = jbase + k;
+                if (row_ok && j <= i) {
+                    if (exact) {
+                        const long long a = (int)(odd ? r0 : own0), bb = (int)(odd ? r1 : own1);
+                        const long long c = (int)(odd ? own0 : r0), d = (int)(odd ? own1 : r1);
+                        unsigned long long *dst = static_cast<unsigned long long *>(J.V) + 2 * (prow + j);
+                        atomicAdd(dst, (unsigned long long)(a + d));
+                        atomicAdd(dst + 1, (unsigned long long)(c - bb));
+                    } else {
+                        const float a = __uint_as_float(odd ? r0 : own0), bb = __uint_as_float(odd ? r1 : own1);
+                        const float c = __uint_as_float(odd ? own0 : r0), d = __uint_as_float(odd ? own1 : r1);
+                        float2 *dst = static_cast<float2 *>(J.V) + (prow + j);
+                        atomicAdd(dst, make_float2((a + d) * J.vscale, (c - bb) * J.vscale));
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 128; ++k) m[k] = 0u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+struct TcPlan {
+    TcParams params;
+    int grid = 0;
+    size_t smem = 0;
+};
+
+bool tc_supported(int device)
+{
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess) return false;
+    return major == 10 && minor == 3;
+}
+
+cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, TcPlan **out, std::string *err)
+{
+    *out = nullptr;
+    if (n_jobs < 1 || n_jobs > kMaxJobs) {
+        if (err) *err = "tensor-core plan: 1..64 jobs";
+        return cudaErrorInvalidValue;
+    }
+    auto enc = encode_fn();
+    if (!enc) {
+        if (err) *err = "cuTensorMapEncodeTiled unavailable";
+        return cudaErrorNotSupported;
+    }
+    TcPlan *p = new TcPlan();
+    std::memset(&p->params, 0, sizeof(p->params));
+    // longest-first order when requested (items of a job are contiguous)
+    std::vector<int> order(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) order[j] = j;
+    auto cost = [&](int j) {
+        return (double)jobs[j].N * jobs[j].N * jobs[j].n_time * (jobs[j].mode == ACF_X_FP16x3 ? 3 : 1);
+    };
+    if (tun.order == 1) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    int items = 0;
+    for (int jj = 0; jj < n_jobs; ++jj) {
+        const TcJob &J = jobs[order[jj]];
+        JobDev &D = p->params.jobs[jj];
+        if (J.t_stride % 64 != 0 || J.N < 1 || J.n_problems < 1 || J.n_time < 0 ||
+            (long)J.n_problems * 2 * J.N >= (1L << 31) || J.t_stride >= (1L << 31)) {
+            delete p;
+            if (err) *err = "tensor-core plan: bad job geometry";
+            return cudaErrorInvalidValue;
+        }
+        D.V = J.V;
+        D.N = J.N;
+        D.n_problems = J.n_problems;
+        D.mode = J.mode;
+        D.nt = (tun.n_tile == 128) ? 128 : 256;
+        D.n_time = J.n_time;
+        const long K64 = round_up(J.n_time, 64);
+        int ks = std::max(1, tun.k_split);
+        if (J.mode == ACF_X_INT8) ks = std::max<long>(ks, (K64 + 65535) / 65536);
+        D.k_split = ks;
+        D.mb = (2 * J.N + kBM - 1) / kBM;
+        D.tiles_pp = tiles_per_problem(J.N, D.nt);
+        D.item_begin = items;
+        D.vscale = J.vscale;
+        items += D.tiles_pp * ks * J.n_problems;
+        for (int h = 0; h < 2; ++h) {
+            const void *base = (h == 0 || !J.x_lo) ? (const void *)J.x : (const void *)J.x_lo;
+            cuuint64_t dims[2] = {(cuuint64_t)J.t_stride, (cuuint64_t)J.n_problems * 2 * J.N};
+            cuuint64_t strides[1] = {(cuuint64_t)J.t_stride * 2};
+            cuuint32_t box[2] = {64, 128};
+            cuuint32_t es[2] = {1, 1};
+            CUresult r = enc(&p->params.maps[jj][h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims,
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                delete p;
+                if (err) *err = "cuTensorMapEncodeTiled failed (alignment or size)";
+                return cudaErrorInvalidValue;
+            }
+        }
+    }
+    p->params.n_jobs = n_jobs;
+    p->params.n_items = items;
+    p->params.err = device_error_word();
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    p->grid = std::max(1, std::min(items, sms));
+    p->smem = (size_t)kSlots * kSlotBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    if (e != cudaSuccess) {
+        delete p;
+        if (err) *err = "cudaFuncSetAttribute(max dynamic smem) failed";
+        return e;
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale)
+{
+    if (job < 0 || job >= p->params.n_jobs) return cudaErrorInvalidValue;
+    p->params.jobs[job].n_time = n_time;
+    p->params.jobs[job].vscale = vscale;
+    return cudaSuccess;
+}
+
+cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
+{
+    if (p->params.n_items == 0) return cudaSuccess;
+    k_xeng_tc<<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+int tc_plan_items(const TcPlan *p) { return p->params.n_items; }
+void tc_plan_destroy(TcPlan *p) { delete p; }
+
+}  // namespace acf
