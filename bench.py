@@ -175,6 +175,27 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
                 launches=launches, ops_per_step=ops / steps)
 
 
+def profile_case(mode):
+    import torch
+
+    import paper_1609_04205_b300 as acf
+    import synth
+    w = dict(synth.WORKLOADS["a6" if mode == "int8" else "a12"])
+    w["n_subbands"] = 1
+    if mode == "int8":
+        w.update(n_channels=1, n_taps=1, dtype="ci8")
+    sky = synth.make_sky(w["n_inputs"], w["n_sources"], w["flux"], w["seed"]) if w["n_sources"] else None
+    x = synth.voltages(w["n_inputs"], w["n_samples"], 1, w["dtype"], w["sigma"], sky, w["seed"], device="cuda")
+    with acf.Correlator(w["n_inputs"], 1, w["n_channels"], w["n_taps"], 1, mode, w["dtype"], w["n_samples"]) as c:
+        out = c.empty_visibilities()
+        for _ in range(4):
+            c.push(x)
+            c.visibilities(out)
+        torch.cuda.synchronize()
+    print("profile case %s done" % mode)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,9 +203,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="acf", choices=["acf", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the comparison modes and the e2e pass")
+    ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8"], default=None,
+                    help="small case for ncu captures: one subband of the default workload (one raw "
+                         "A-6 subband for int8), warm-up plus three pushes, no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args.profile_case)
 
     import torch
 

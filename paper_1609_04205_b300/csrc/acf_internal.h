@@ -31,6 +31,16 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
                               const float *bandpass, const float2 *tw, int out_kind, void *out,
                               void *out_lo, long t_stride, float scale, long T,
                               cudaStream_t s);
+// General kernel (any supported C, P, dtype); launch_channelise picks the fast path when it applies.
+cudaError_t launch_channelise_generic(const void *hist, long n_hist, const void *samples, long n_samples,
+                                      acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
+                                      const float *bandpass, const float2 *tw, int out_kind, void *out,
+                                      void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
+// Fast path (chan_fast.cu): 16 taps, 16 or 64 channels, ci8 / ci16 input.
+bool chan_fast_supported(acf_in_dtype dt, int C, int P);
+cudaError_t launch_chan_fast(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
+                             int n_sb, int N, int C, const float *h, const float *bp, const float2 *tw, int out_kind,
+                             void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
 cudaError_t launch_transpose_raw(const void *samples, long n_samples, acf_in_dtype dt, int n_sb,
                                  int N, int out_kind, void *out, void *out_lo, long t_stride,
                                  float scale, cudaStream_t s);
@@ -55,6 +65,7 @@ struct TcJob {
     long t_stride;        // row stride in elements
     int mode;             // ACF_X_FP16, ACF_X_FP16x3 or ACF_X_INT8
     float vscale;
+    int store = 0;        // 1: overwrite V (allowed only when one work item owns each tile)
 };
 struct TcPlan;            // opaque: tensor maps + work list on the device
 struct TcTuning {
@@ -65,8 +76,11 @@ struct TcTuning {
 cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, TcPlan **out,
                            std::string *err);
 cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s);
-// Per-launch job parameters: valid spectra and the fp result scale.
-cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale);
+// Per-launch job parameters: valid spectra, the fp result scale, and whether
+// the launch may overwrite V (granted only when the job has no time split).
+cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale, int store);
+int tc_plan_job_stores(const TcPlan *p, int job);   // 1 when the job overwrites V
+int tc_plan_job_split(const TcPlan *p, int job);
 int tc_plan_items(const TcPlan *p);
 void tc_plan_destroy(TcPlan *p);
 bool tc_supported(int device);

@@ -92,6 +92,7 @@ static std::vector<TcJob> tc_jobs(const acf_batch *b, void *const *outputs)
         j.t_stride = b->t_stride[k];
         j.mode = raw ? ACF_X_INT8 : ACF_X_FP16x3;
         j.vscale = raw ? 1.f : 1.f / (b->scale[k] * b->scale[k]);
+        j.store = 1;      // each run is a fresh integration: overwrite when the tiles are unsplit
     }
     return v;
 }
@@ -102,7 +103,8 @@ static cudaError_t enqueue_all(acf_batch *b, const void *const *inputs, void *co
     cudaError_t e;
     for (size_t k = 0; k < b->jobs.size(); ++k) {
         const acf_job &J = b->jobs[k];
-        if ((e = cudaMemsetAsync(outputs[k], 0, b->v_bytes[k], s)) != cudaSuccess) return e;
+        if (b->T[k] == 0 || !tc_plan_job_stores(b->plan, (int)k))
+            if ((e = cudaMemsetAsync(outputs[k], 0, b->v_bytes[k], s)) != cudaSuccess) return e;
         if (b->T[k] == 0) continue;
         if (J.n_channels == 1) {
             e = launch_transpose_raw(inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, OUT_F16, b->X[k], nullptr,

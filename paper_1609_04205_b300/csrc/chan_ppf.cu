@@ -342,6 +342,18 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
                               const float *bandpass, const float2 *tw, int out_kind, void *out,
                               void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
 {
+    if (chan_fast_supported(dt, C, P))
+        return launch_chan_fast(hist, n_hist, samples, n_samples, dt, n_sb, N, C, h, bandpass, tw, out_kind, out,
+                                out_lo, t_stride, scale, T, s);
+    return launch_channelise_generic(hist, n_hist, samples, n_samples, dt, n_sb, N, C, P, h, bandpass, tw, out_kind,
+                                     out, out_lo, t_stride, scale, T, s);
+}
+
+cudaError_t launch_channelise_generic(const void *hist, long n_hist, const void *samples, long n_samples,
+                                      acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
+                                      const float *bandpass, const float2 *tw, int out_kind, void *out,
+                                      void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
+{
     switch (dt) {
     case ACF_IN_CI8:  return launch_by_c<char2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, s);
     case ACF_IN_CI16: return launch_by_c<short2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, s);

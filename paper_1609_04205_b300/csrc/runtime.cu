@@ -69,6 +69,7 @@ struct acf_ctx {
     TcPlan *plan = nullptr;
     int pushes = 0;
     bool ready = false;
+    bool v_valid = false;         // V already holds this integration's partial sums
     long last_T = 0;
     bool timing = false, timed = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -315,8 +316,6 @@ static acf_status push_common(acf_ctx *c, const void *dev_samples, long S, cudaS
     const long L = (long)c->P * c->C;
     const int out_kind = c->mode == ACF_X_FP32 ? OUT_F32 : (c->mode == ACF_X_FP16x3 ? OUT_F16X3 : OUT_F16);
     const float scale = (c->mode == ACF_X_FP16 || c->mode == ACF_X_FP16x3) ? c->scale : 1.f;
-    if (c->pushes == 0 && (e = cudaMemsetAsync(c->d_V, 0, c->v_bytes, s)) != cudaSuccess)
-        return cuda_fail(c, e, "clear accumulator");
     if (c->timing) cudaEventRecord(c->ev[0], s);
     long T;
     const size_t xelem = c->mode == ACF_X_FP32 ? 4 : 2;
@@ -363,11 +362,21 @@ static acf_status push_common(acf_ctx *c, const void *dev_samples, long S, cudaS
     }
     if (c->timing) cudaEventRecord(c->ev[1], s);
     if (T > 0) {
+        // the first X-engine pass of an integration overwrites V when one work item owns
+        // each tile; otherwise V is cleared and every pass adds atomically
+        bool clear = !c->v_valid;
+        if (c->mode != ACF_X_FP32) {
+            if ((e = tc_plan_set_job(c->plan, 0, T, 1.f / (scale * scale), c->v_valid ? 0 : 1)) != cudaSuccess)
+                return cuda_fail(c, e, "x-engine plan");
+            if (tc_plan_job_stores(c->plan, 0)) clear = false;
+        }
+        if (clear && (e = cudaMemsetAsync(c->d_V, 0, c->v_bytes, s)) != cudaSuccess)
+            return cuda_fail(c, e, "clear accumulator");
+        c->v_valid = true;
         if (c->mode == ACF_X_FP32) {
             e = launch_xeng_simt(static_cast<const float *>(c->d_X), c->n_sb * c->C, c->N, T, c->t_stride, 1.f,
                                  static_cast<float2 *>(c->d_V), s);
         } else {
-            tc_plan_set_job(c->plan, 0, T, 1.f / (scale * scale));
             e = tc_plan_launch(c->plan, s);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "x-engine");
@@ -380,6 +389,10 @@ static acf_status push_common(acf_ctx *c, const void *dev_samples, long S, cudaS
     if (++c->pushes == c->n_integrate) {
         c->pushes = 0;
         c->ready = true;
+        if (!c->v_valid) {   // an integration without a single spectrum is all zeros
+            if ((e = cudaMemsetAsync(c->d_V, 0, c->v_bytes, s)) != cudaSuccess) return cuda_fail(c, e, "clear");
+            c->v_valid = true;
+        }
     }
     return ACF_OK;
 }
@@ -441,6 +454,7 @@ acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_
     if (e != cudaSuccess) return cuda_fail(c, e, "copy visibilities");
     *n_ready = 1;
     c->ready = false;
+    c->v_valid = false;
     return ACF_OK;
 }
 
@@ -562,6 +576,9 @@ acf_status acf_xengine(acf_xmode mode, const void *x, const void *x_lo, int n_pr
                        long t_stride, float vscale, void *V, acf_stream_t stream)
 {
     if (!x || !V || n_problems < 1 || n_inputs < 1 || n_time < 0 || t_stride % 64 != 0 || t_stride < round_up(n_time, 64))
+        return ACF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(V) % 16 != 0 || reinterpret_cast<uintptr_t>(x) % 16 != 0 ||
+        (x_lo && reinterpret_cast<uintptr_t>(x_lo) % 16 != 0))
         return ACF_EINVAL;
     if (mode < ACF_X_FP32 || mode > ACF_X_INT8) return ACF_EINVAL;
     if (mode == ACF_X_FP16x3 && !x_lo) return ACF_EINVAL;

@@ -47,6 +47,10 @@ constexpr int kThreadsTc = 320;
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitLimit = 1LL << 22;   // x 256 ns back-off: about one second
+// INT8 work items span at most 2^15 samples: int32 register sums of |x| <= 128
+// products stay below 2^29, so masters and their 2x2 combine are exact.
+constexpr long kInt8ItemMax = 32768;
+constexpr int kPfSteps = 12;                  // L2 prefetch distance in K steps
 
 struct JobDev {
     void *V;
@@ -54,6 +58,7 @@ struct JobDev {
     long n_time;
     int k_split, tiles_pp, mb, item_begin;
     float vscale;
+    int store;            // 1: each visibility written once with plain stores; 0: atomically added
 };
 
 struct TcParams {
@@ -114,6 +119,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
         : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -194,9 +205,13 @@ __device__ __forceinline__ bool decode_item(const TcParams &P, int item, Item &i
     return it.k0 < it.k1;
 }
 
-__device__ __forceinline__ int chunk_steps(int mode) {
-    return mode == ACF_X_INT8 ? 8 : (mode == ACF_X_FP16x3 ? 16 : (1 << 30));
-}
+// The TMEM accumulator is drained into register sums every few K steps.  INT8
+// needs 512-sample chunks for exactness (partial sums < 2^23).  The tensor
+// core's fp32 accumulation rounds toward zero, so short chunks folded into
+// round-to-nearest register sums bound the float modes' bias: 512 samples
+// (32 MMAs, <= 2^-18 relative) for split FP16, 1024 samples (<= 2^-17) for
+// plain FP16, whose operand rounding (2^-11) dominates anyway.
+__device__ __forceinline__ int chunk_steps(int mode) { return mode == ACF_X_FP16 ? 16 : 8; }
 
 __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant__ TcParams P)
 {
@@ -242,6 +257,40 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             }
             long pos = 0;
             bool ok = true;
+            // L2 prefetch cursor: kPfSteps K steps ahead of the loads, running on into
+            // this CTA's next work item, so first touches of X come from L2, not DRAM
+            int pf_item = blockIdx.x;
+            Item pf;
+            bool pf_ok = false;
+            long pf_k = 0;
+            auto pf_seek = [&]() {
+                while (pf_item < P.n_items) {
+                    if (decode_item(P, pf_item, pf)) {
+                        pf_ok = true;
+                        pf_k = pf.k0;
+                        return;
+                    }
+                    pf_item += gridDim.x;
+                }
+                pf_ok = false;
+            };
+            auto pf_step = [&]() {
+                if (!pf_ok) return;
+                const JobDev &Jp = P.jobs[pf.job];
+                const int rA = pf.p * 2 * Jp.N + pf.bi * kBM, rB = pf.p * 2 * Jp.N + pf.bj * Jp.nt;
+                for (int h = 0; h < (Jp.mode == ACF_X_FP16x3 ? 2 : 1); ++h) {
+                    const CUtensorMap *mp = &P.maps[pf.job][h];
+                    tma_prefetch_2d(mp, (int)pf_k, rA);
+                    for (int q = 0; q < Jp.nt / kBM; ++q) tma_prefetch_2d(mp, (int)pf_k, rB + q * kBM);
+                }
+                pf_k += kBK;
+                if (pf_k >= pf.k1) {
+                    pf_item += gridDim.x;
+                    pf_seek();
+                }
+            };
+            pf_seek();
+            for (int s = 0; s < kPfSteps; ++s) pf_step();
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
                 Item it;
                 if (!decode_item(P, item, it)) continue;
@@ -251,6 +300,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
                 const int rowB = it.p * 2 * J.N + it.bj * J.nt;
                 const uint32_t bytes = (uint32_t)(kBM + J.nt) * kBK * 2;
                 for (long k = it.k0; k < it.k1 && ok; k += kBK) {
+                    pf_step();
                     for (int h = 0; h < spk && ok; ++h) {
                         const int slot = (int)(pos % kSlots);
                         const uint32_t ph = (uint32_t)((pos / kSlots) & 1);
@@ -383,12 +433,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             }
             if (!ok) break;
             if (!active) continue;
-            // flush: combine 2x2 real blocks into complex visibilities
+            // flush: combine 2x2 real blocks into complex visibilities, in place:
+            // after iteration k, m[2k], m[2k+1] hold (Re, Im) of V[i][jbase + k]
             const int i = it.bi * 64 + 16 * q + (lane >> 1);
             const int jbase = (J.nt * it.bj + 128 * half) / 2 + 32 * odd;
             const long NB = (long)J.N * (J.N + 1) / 2;
             const long prow = (long)it.p * NB + (long)i * (i + 1) / 2;
-            const bool row_ok = i < J.N;
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const uint32_t s0v = odd ? m[2 * k] : m[64 + 2 * k];
@@ -397,21 +447,52 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
                 const uint32_t r1 = __shfl_xor_sync(0xffffffffu, s1v, 1);
                 const uint32_t own0 = odd ? m[64 + 2 * k] : m[2 * k];
                 const uint32_t own1 = odd ? m[65 + 2 * k] : m[2 * k + 1];
-                // even lane: a = own0, b = own1, c = r0, d = r1
-                // odd lane:  c = own0, d = own1, a = r0, b = r1
-                const int j = jbase + k;
-                if (row_ok && j <= i) {
-                    if (exact) {
-                        const long long a = (int)(odd ? r0 : own0), bb = (int)(odd ? r1 : own1);
-                        const long long c = (int)(odd ? own0 : r0), d = (int)(odd ? own1 : r1);
-                        unsigned long long *dst = static_cast<unsigned long long *>(J.V) + 2 * (prow + j);
-                        atomicAdd(dst, (unsigned long long)(a + d));
-                        atomicAdd(dst + 1, (unsigned long long)(c - bb));
-                    } else {
-                        const float a = __uint_as_float(odd ? r0 : own0), bb = __uint_as_float(odd ? r1 : own1);
-                        const float c = __uint_as_float(odd ? own0 : r0), d = __uint_as_float(odd ? own1 : r1);
-                        float2 *dst = static_cast<float2 *>(J.V) + (prow + j);
-                        atomicAdd(dst, make_float2((a + d) * J.vscale, (c - bb) * J.vscale));
+                // even lane: a = own0, b = own1, c = r0, d = r1; odd lane: c, d own, a, b received
+                const uint32_t a = odd ? r0 : own0, bq = odd ? r1 : own1;
+                const uint32_t c = odd ? own0 : r0, d = odd ? own1 : r1;
+                if (exact) {
+                    // exact in int32: items span <= 32,768 samples, so |D| <= 128^2 * 2^15 = 2^29
+                    m[2 * k] = (uint32_t)((int)a + (int)d);
+                    m[2 * k + 1] = (uint32_t)((int)c - (int)bq);
+                } else {
+                    m[2 * k] = __float_as_uint((__uint_as_float(a) + __uint_as_float(d)) * J.vscale);
+                    m[2 * k + 1] = __float_as_uint((__uint_as_float(c) - __uint_as_float(bq)) * J.vscale);
+                }
+            }
+            // valid run of this lane: j in [jbase, min(jbase + 32, i + 1)), row i < N
+            const int nval = (i < J.N) ? max(0, min(32, i + 1 - jbase)) : 0;
+            if (nval > 0) {
+                if (exact) {
+                    long long *dst = static_cast<long long *>(J.V) + 2 * (prow + jbase);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        if (k < nval) {
+                            const long long re = (int)m[2 * k], im = (int)m[2 * k + 1];
+                            if (J.store) {
+                                *reinterpret_cast<longlong2 *>(dst + 2 * k) = make_longlong2(re, im);
+                            } else {
+                                atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k), (unsigned long long)re);
+                                atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k + 1), (unsigned long long)im);
+                            }
+                        }
+                    }
+                } else {
+                    float2 *dst = static_cast<float2 *>(J.V) + (prow + jbase);
+                    // pair elements on 16-byte boundaries: a leading single when the run starts odd
+                    const int lead = (int)((prow + jbase) & 1);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float2 v0 = make_float2(__uint_as_float(m[2 * k]), __uint_as_float(m[2 * k + 1]));
+                        const bool single = (k == 0 && lead) || (k + 1 == nval && ((k - lead) & 1) == 0);
+                        const bool pair_start = !single && ((k - lead) & 1) == 0 && k + 1 < nval;
+                        if (k < nval && single) {
+                            if (J.store) dst[k] = v0;
+                            else atomicAdd(dst + k, v0);
+                        } else if (k < 31 && k < nval && pair_start) {
+                            const float4 v = make_float4(v0.x, v0.y, __uint_as_float(m[2 * k + 2]), __uint_as_float(m[2 * k + 3]));
+                            if (J.store) *reinterpret_cast<float4 *>(dst + k) = v;
+                            else atomicAdd(reinterpret_cast<float4 *>(dst + k), v);
+                        }
                     }
                 }
             }
@@ -445,6 +526,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 struct TcPlan {
     TcParams params;
+    int slot_of[kMaxJobs];   // caller's job index -> position in the work list
     int grid = 0;
     size_t smem = 0;
 };
@@ -496,12 +578,14 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
         D.n_time = J.n_time;
         const long K64 = round_up(J.n_time, 64);
         int ks = std::max(1, tun.k_split);
-        if (J.mode == ACF_X_INT8) ks = std::max<long>(ks, (K64 + 65535) / 65536);
+        if (J.mode == ACF_X_INT8) ks = std::max<long>(ks, (K64 + kInt8ItemMax - 1) / kInt8ItemMax);
         D.k_split = ks;
         D.mb = (2 * J.N + kBM - 1) / kBM;
         D.tiles_pp = tiles_per_problem(J.N, D.nt);
         D.item_begin = items;
         D.vscale = J.vscale;
+        D.store = (J.store && ks == 1) ? 1 : 0;
+        p->slot_of[order[jj]] = jj;
         items += D.tiles_pp * ks * J.n_problems;
         for (int h = 0; h < 2; ++h) {
             const void *base = (h == 0 || !J.x_lo) ? (const void *)J.x : (const void *)J.x_lo;
@@ -537,13 +621,23 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
     return cudaSuccess;
 }
 
-cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale)
+cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale, int store)
 {
     if (job < 0 || job >= p->params.n_jobs) return cudaErrorInvalidValue;
-    p->params.jobs[job].n_time = n_time;
-    p->params.jobs[job].vscale = vscale;
+    JobDev &D = p->params.jobs[p->slot_of[job]];
+    const long K64 = round_up(n_time, 64);
+    const long old64 = round_up(D.n_time, 64);
+    // the time split was sized for the planned length; refuse a longer one
+    if (D.mode == ACF_X_INT8 && (K64 + D.k_split - 1) / D.k_split > kInt8ItemMax) return cudaErrorInvalidValue;
+    (void)old64;
+    D.n_time = n_time;
+    D.vscale = vscale;
+    D.store = (store && D.k_split == 1) ? 1 : 0;
     return cudaSuccess;
 }
+
+int tc_plan_job_stores(const TcPlan *p, int job) { return p->params.jobs[p->slot_of[job]].store; }
+int tc_plan_job_split(const TcPlan *p, int job) { return p->params.jobs[p->slot_of[job]].k_split; }
 
 cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
 {
