@@ -175,6 +175,23 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
                 launches=launches, ops_per_step=ops / steps)
 
 
+def aggregate(ms_local, ops_local, device="cpu"):
+    """Whole-job figures across ranks: step time = max over ranks, value =
+    the ops of all ranks over that time (weak scaling: each rank correlates
+    its own subband set; no data moves between ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, ops_local / (ms_local * 1e-3) / 1e12
+    t = torch.tensor([ms_local, ops_local], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms = float(mx[0].item())
+    return ms, float(tot[1].item()) / (ms * 1e-3) / 1e12
+
+
 def profile_case(mode):
     import torch
 
@@ -240,12 +257,7 @@ def main():
     clk = Clocks(local)
     main_r = time_mode(acf, torch, x, w, "fp16", args.steps, args.warmup, stream)
     clocks = clk.stop()
-    ms = main_r["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = main_r["ops_per_step"] * world / (ms * 1e-3) / 1e12
+    ms, value = aggregate(main_r["ms_per_step"], main_r["ops_per_step"], dev)
 
     extra = {}
     if not args.quick:
