@@ -27,7 +27,7 @@ EXPORTS = [
     "acf_status_string", "acf_prototype", "acf_channelise", "acf_transpose_raw", "acf_xengine",
     "acf_gain_forward", "acf_gain_backward", "acf_batch_create", "acf_batch_run", "acf_batch_query",
     "acf_batch_destroy", "acf_batch_last_error", "acf_launch_count", "acf_device_status", "acf_version",
-    "acf_enable_timing", "acf_last_timing",
+    "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
         "acf_version": ([], ctypes.c_char_p),
         "acf_enable_timing": ([P, I], I),
         "acf_last_timing": ([P, ctypes.POINTER(F), ctypes.POINTER(F)], I),
+        "acf_gain_forward_noalloc": ([P, P, P, I, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

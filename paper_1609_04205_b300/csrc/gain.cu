@@ -13,6 +13,8 @@
 // and one global atomic per (tile row/column) lands in grad.  The per-block
 // loss partials are summed by a second, single-block kernel in a fixed order,
 // so the loss is deterministic.
+#include <mutex>
+
 #include "acf_internal.h"
 
 namespace acf {
@@ -156,3 +158,58 @@ cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N
 }
 
 }  // namespace acf
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of acf_gain_forward for callers that cannot call
+// cudaMalloc: code running inside a CUDA-graph capture or under a strict
+// memory budget, embedded hosts whose device memory is carved up in advance,
+// or plug-ins of a framework that owns all allocations.  The loss partials
+// live in a fixed array in this library's device image instead of a buffer
+// the library allocates.  Every GPU that loads the library holds the array
+// (kGainStaticPartials floats) until the process exits.
+// ---------------------------------------------------------------------------
+namespace acf {
+namespace {
+constexpr int kGainStaticPartials = 65536;          // 256 KiB of loss partials
+static __device__ __align__(256) float g_gain_static_partials[kGainStaticPartials];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+float *g_static_ptr[kMaxDevices] = {nullptr};        // device address per device, set once
+
+// Device address of the static array for the current device.  Host code may not
+// use the symbol itself (it is a host-side stand-in, not a device pointer).
+cudaError_t static_partials(float **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_gain_static_partials);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+}  // namespace acf
+
+extern "C" acf_status acf_gain_forward_noalloc(const void *R, const void *V, const void *g, int n_inputs,
+                                               int n_channels, float *loss, void *grad, acf_stream_t stream)
+{
+    using namespace acf;
+    if (!R || !V || !g || n_inputs < 1 || n_channels < 1 || (!loss && !grad)) return ACF_EINVAL;
+    const long need = (long)gain_partials_needed(n_inputs, n_channels);
+    if (need > kGainStaticPartials) return ACF_EINVAL;       // beyond the fixed scratch
+    float *part = nullptr;
+    if (static_partials(&part) != cudaSuccess) return ACF_ECUDA;
+    cudaError_t e = launch_gain(static_cast<const float2 *>(R), static_cast<const float2 *>(V),
+                                static_cast<const float2 *>(g), n_inputs, n_channels, loss,
+                                static_cast<float2 *>(grad), part, kGainStaticPartials, (cudaStream_t)stream);
+    return e == cudaSuccess ? ACF_OK : ACF_ECUDA;
+}
+
