@@ -42,6 +42,26 @@ def peaks():
     return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
 
 
+def xeng_traffic_per_subband():
+    """DRAM bytes per subband of the X-engine launch from the committed ncu
+    summary, valid only while the kernel source is the one that was captured
+    (one-subband capture, scaled by subbands: traffic grows in proportion)."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "xeng_tc_chan64_fp16_a12_1subband.md")
+    src = os.path.join(ROOT, "paper_1609_04205_b300", "csrc", "xeng_tc.cu")
+    try:
+        txt = open(prof).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = re.search(r"xeng_tc.cu sha256 prefix `([0-9a-f]+)`", txt)
+        t = re.search(r"traffic_per_subband_bytes k_xeng_tc: (\d+)", txt)
+        if m and t and m.group(1) == h:
+            return int(t.group(1))
+    except OSError:
+        pass
+    return None
+
+
 def xops(N, T, n_ch, n_sb):
     """Algorithmic X-engine ops: one complex MAC (8 real ops) per baseline per spectrum."""
     return 8.0 * N * (N + 1) / 2 * T * n_ch * n_sb
@@ -324,8 +344,9 @@ def main():
 
     xeng_ms = main_r["xeng_ms"]
     achieved = main_r["xeng_tops"]
+    tps = xeng_traffic_per_subband()
     roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16_sus"], unit="TFLOP/s",
-                frac=achieved / pk["bf16_sus"], traffic=None,
+                frac=achieved / pk["bf16_sus"], traffic=None if tps is None else tps * n_sb,
                 note="X-engine (k_xeng_tc, FP16 operands, fp32 accumulation); algorithmic ops "
                      "8*N(N+1)/2*spectra*channels*subbands = %.3e per launch over its CUDA-event time %.3f ms; "
                      "peak = %s bf16 sustained (fp16 dense = bf16 dense on B300); frac of burst %.3f"
