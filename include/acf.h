@@ -141,6 +141,12 @@ acf_status acf_query(acf_ctx *ctx, long *last_spectra, long *t_stride, float *sc
 acf_status acf_enable_timing(acf_ctx *ctx, int on);
 acf_status acf_last_timing(acf_ctx *ctx, float *chan_ms, float *xeng_ms);
 
+/* Tensor-core X-engine variant for this context: 0 = one SM per 128x256 tile,
+ * 1 = SM pairs (clusters of two CTAs) per 256x256 tile, each SM loading half
+ * of both operands.  Rebuilds the launch plan; only between integrations.
+ * EINVAL for other values, ESTATE mid-integration or in FP32 mode. */
+acf_status acf_set_xengine_variant(acf_ctx *ctx, int variant);
+
 /* Release every resource.  Synchronises the device first.  NULL is a no-op. */
 acf_status acf_destroy(acf_ctx *ctx);
 

@@ -27,7 +27,7 @@ EXPORTS = [
     "acf_status_string", "acf_prototype", "acf_channelise", "acf_transpose_raw", "acf_xengine",
     "acf_gain_forward", "acf_gain_backward", "acf_batch_create", "acf_batch_run", "acf_batch_query",
     "acf_batch_destroy", "acf_batch_last_error", "acf_launch_count", "acf_device_status", "acf_version",
-    "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc",
+    "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc", "acf_set_xengine_variant",
 ]
 
 
@@ -92,6 +92,7 @@ def lib():
         "acf_enable_timing": ([P, I], I),
         "acf_last_timing": ([P, ctypes.POINTER(F), ctypes.POINTER(F)], I),
         "acf_gain_forward_noalloc": ([P, P, P, I, I, P, P, P], I),
+        "acf_set_xengine_variant": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

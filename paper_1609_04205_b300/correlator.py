@@ -25,7 +25,7 @@ class Correlator:
     pairs in INT8 mode)."""
 
     def __init__(self, n_inputs, n_subbands=1, n_channels=64, n_taps=16, n_integrate=1,
-                 mode="fp32", dtype="ci8", max_samples=1 << 16):
+                 mode="fp32", dtype="ci8", max_samples=1 << 16, variant=None):
         self._L = A.lib()
         self.n_inputs, self.n_subbands, self.n_channels = n_inputs, n_subbands, n_channels
         self.n_taps, self.n_integrate, self.mode, self.dtype = n_taps, n_integrate, mode, dtype
@@ -35,6 +35,8 @@ class Correlator:
                                 A.MODES[mode], A.DTYPES[dtype], max_samples)
         A.check(st, None)
         self._h = h
+        if variant is not None:
+            self.set_xengine_variant(variant)
 
     # -- lifecycle
     def close(self):
@@ -59,6 +61,10 @@ class Correlator:
         import numpy as np
         w = np.ascontiguousarray(w, dtype=np.float32)
         A.check(self._L.acf_set_bandpass(self._h, w.ctypes.data_as(ctypes.c_void_p)), self._h)
+
+    def set_xengine_variant(self, variant: int):
+        """0: one SM per tile; 1: SM pairs sharing each 256x256 tile (cta_group::2)."""
+        A.check(self._L.acf_set_xengine_variant(self._h, int(variant)), self._h)
 
     def set_input_scale(self, s: float):
         A.check(self._L.acf_set_input_scale(self._h, float(s)), self._h)

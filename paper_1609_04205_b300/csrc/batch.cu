@@ -50,6 +50,13 @@ void proto(int P, int C, std::vector<float> &h)
 
 using namespace acf;
 
+static TcTuning default_tuning()
+{
+    TcTuning t;
+    t.pair = 0;        // one SM per tile; the autotuner also tries SM pairs
+    return t;
+}
+
 struct acf_batch {
     std::vector<acf_job> jobs;
     std::vector<long> T, t_stride;
@@ -59,7 +66,7 @@ struct acf_batch {
     std::map<long, float *> d_h;        // key P*1024 + C
     std::map<int, float2 *> d_tw;       // key C
     std::map<int, float *> d_bp;        // key C (all ones)
-    TcTuning tun;
+    TcTuning tun = default_tuning();
     TcPlan *plan = nullptr;
     cudaStream_t s_int = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -148,10 +155,13 @@ static void autotune(acf_batch *b)
     cudaEventCreate(&e1);
     float best = 1e30f;
     TcTuning best_t = b->tun;
+    for (int pair : {1, 0})
     for (int nt : {256, 128})
         for (int ks : {1, 2, 4})
             for (int order : {1, 0}) {
+                if (pair && nt == 128) continue;   // the pair kernel always uses 256-row tiles
                 TcTuning t;
+                t.pair = pair;
                 t.n_tile = nt;
                 t.k_split = ks;
                 t.order = order;

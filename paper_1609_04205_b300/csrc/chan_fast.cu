@@ -89,11 +89,14 @@ k_chan_fast(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in,
     const IN *isb = in + (long)sb * n_samples * N;
 
     // per-thread constants: taps, twiddles, bandpass * scale
-    float hr[R][kP];
+    float2 hr[R][kP];           // (h, h) pairs for packed fp32x2 FMAs
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < kP; ++k) hr[r][k] = __ldg(h + k * C + ql + L * r);
+        for (int k = 0; k < kP; ++k) {
+            const float hv = __ldg(h + k * C + ql + L * r);
+            hr[r][k] = make_float2(hv, hv);
+        }
     // stage LB (span L): W_C^{ql}; stage s < LB (span 2^s): W_{2^{s+1}}^{ql mod 2^s}
     const float2 tw_top = tw[ql];
     float2 tws[LB > 0 ? LB : 1];
@@ -164,16 +167,13 @@ k_chan_fast(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in,
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 win[r][(mm + kP - 1) % kP] = tof2(sin[il * G::ROWI + mm * C + ql + L * r]);
-                float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < kP; k += 2) {
-                    const float2 x0 = win[r][(mm + k) % kP], x1 = win[r][(mm + k + 1) % kP];
-                    ax = fmaf(hr[r][k], x0.x, ax);
-                    ay = fmaf(hr[r][k], x0.y, ay);
-                    bx = fmaf(hr[r][k + 1], x1.x, bx);
-                    by = fmaf(hr[r][k + 1], x1.y, by);
+                    a0 = __ffma2_rn(hr[r][k], win[r][(mm + k) % kP], a0);
+                    a1 = __ffma2_rn(hr[r][k + 1], win[r][(mm + k + 1) % kP], a1);
                 }
-                z[r] = make_float2(ax + bx, ay + by);
+                z[r] = __fadd2_rn(a0, a1);
             }
             // stage LB: the thread's own pair (q, q + L)
             {
@@ -264,8 +264,9 @@ k_chan_fast(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in,
 //   pass 1: for s < 8:   Z_s[k1] = sum_r y[s + 8r] W_8^{r k1} * W_64^{s k1} -> slot s + 8 k1
 //   pass 2: for k1 < 8:  X[k1 + 8 k2] = sum_s Z_s[k1] W_8^{s k2}
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add / subtract as one packed fp32x2 operation each.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }   // * (-i)
 
 // In-register 8-point DFT, natural-order output: A[k] = sum_r a[r] exp(-2 pi i r k / 8).
@@ -360,9 +361,12 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
         stw[tid] = tw_g[tid];
         sbp[tid] = __ldg(bp + tid) * (OUTK == OUT_F32 ? 1.f : scale);
     }
-    float hr[kP];
+    float2 hr[kP];              // (h, h): one packed fp32x2 FMA per tap updates (re, im)
 #pragma unroll
-    for (int k = 0; k < kP; ++k) hr[k] = __ldg(h + k * C + q);
+    for (int k = 0; k < kP; ++k) {
+        const float hv = __ldg(h + k * C + q);
+        hr[k] = make_float2(hv, hv);
+    }
 
     using V = typename VecT<G::VB>::T;
     V pre[G::VPT];
@@ -435,16 +439,13 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
 #pragma unroll
         for (int mm = 0; mm < kMB; ++mm) {
             win[(mm + kP - 1) % kP] = tof2(sin[il * G::ROWI + mm * C + q]);
-            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < kP; k += 2) {
-                const float2 x0 = win[(mm + k) % kP], x1 = win[(mm + k + 1) % kP];
-                ax = fmaf(hr[k], x0.x, ax);
-                ay = fmaf(hr[k], x0.y, ay);
-                bx = fmaf(hr[k + 1], x1.x, bx);
-                by = fmaf(hr[k + 1], x1.y, by);
+                a0 = __ffma2_rn(hr[k], win[(mm + k) % kP], a0);
+                a1 = __ffma2_rn(hr[k + 1], win[(mm + k + 1) % kP], a1);
             }
-            yw[mm * G::YROW + q] = make_float2(ax + bx, ay + by);
+            yw[mm * G::YROW + q] = __fadd2_rn(a0, a1);
         }
         __syncthreads();
         // pass 1: thread -> (mm = idx % 16, s = idx / 16), idx = q + 64 j
@@ -476,7 +477,8 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
             for (int k2 = 0; k2 < 8; ++k2) {
                 const int c = k1 + 8 * k2;
                 const float wc = sbp[c];
-                const float re = a[k2].x * wc, im = a[k2].y * wc;
+                const float2 v = __fmul2_rn(a[k2], make_float2(wc, wc));
+                const float re = v.x, im = v.y;
                 if (OUTK == OUT_F32) {
                     reinterpret_cast<float2 *>(sout)[orow + c] = make_float2(re, im);
                 } else {

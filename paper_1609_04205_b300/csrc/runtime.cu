@@ -67,6 +67,7 @@ struct acf_ctx {
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> ev_copied;
     TcPlan *plan = nullptr;
+    int variant = 0;              // one SM per tile (measured faster than SM pairs)
     int pushes = 0;
     bool ready = false;
     bool v_valid = false;         // V already holds this integration's partial sums
@@ -130,9 +131,51 @@ static long spectra_for(long len, int P, int C)
     return len < L ? 0 : (len - L) / C + 1;
 }
 
+static cudaError_t make_plan(acf_ctx *c, std::string *perr)
+{
+    if (c->plan) {
+        tc_plan_destroy(c->plan);
+        c->plan = nullptr;
+    }
+    const long L = (long)c->P * c->C;
+    TcJob j;
+    j.x = static_cast<const __half *>(c->d_X);
+    j.x_lo = static_cast<const __half *>(c->d_Xlo);
+    j.V = c->d_V;
+    j.N = c->N;
+    j.n_problems = c->n_sb * c->C;
+    j.n_time = c->C == 1 ? c->max_samples : spectra_for(L - 1 + c->max_samples, c->P, c->C);
+    j.t_stride = c->t_stride;
+    j.mode = c->mode;
+    j.vscale = 1.f / (c->scale * c->scale);
+    TcTuning tun;
+    tun.pair = c->variant;
+    return tc_plan_create(&j, 1, tun, &c->plan, perr);
+}
+
 extern "C" {
 
 const char *acf_version(void) { return "acf 0.1 (sm_103a)"; }
+
+acf_status acf_set_xengine_variant(acf_ctx *c, int variant)
+{
+    if (!c) return ACF_EINVAL;
+    if (variant != 0 && variant != 1) return fail(c, ACF_EINVAL, "variant must be 0 or 1");
+    if (c->mode == ACF_X_FP32) return fail(c, ACF_ESTATE, "the FP32 path has no tensor-core variant");
+    if (c->pushes != 0) return fail(c, ACF_ESTATE, "variant can only change between integrations");
+    if (variant == c->variant) return ACF_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    const int old = c->variant;
+    c->variant = variant;
+    std::string perr;
+    if ((e = make_plan(c, &perr)) != cudaSuccess) {
+        c->variant = old;
+        make_plan(c, &perr);
+        return fail(c, ACF_ECUDA, "tensor-core plan: " + perr);
+    }
+    return ACF_OK;
+}
 
 long long acf_launch_count(void) { return g_launches.load(); }
 
@@ -251,19 +294,8 @@ acf_status acf_create(acf_ctx **out, int n_inputs, int n_subbands, int n_channel
         return fail(nullptr, ACF_ENOMEM, "device error word");
     }
     if (mode != ACF_X_FP32) {
-        TcJob j;
-        j.x = static_cast<const __half *>(c->d_X);
-        j.x_lo = static_cast<const __half *>(c->d_Xlo);
-        j.V = c->d_V;
-        j.N = n_inputs;
-        j.n_problems = n_subbands * n_channels;
-        j.n_time = Tmax;
-        j.t_stride = c->t_stride;
-        j.mode = mode;
-        j.vscale = 1.f / (c->scale * c->scale);
-        TcTuning tun;
         std::string perr;
-        e = tc_plan_create(&j, 1, tun, &c->plan, &perr);
+        e = make_plan(c, &perr);
         if (e != cudaSuccess) {
             acf_destroy(c);
             return fail(nullptr, ACF_ECUDA, "tensor-core plan: " + perr);

@@ -46,7 +46,8 @@ constexpr int kBM = 128, kBK = 64;
 constexpr int kThreadsTc = 320;
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitLimit = 1LL << 22;   // x 256 ns back-off: about one second
+constexpr long long kWaitLimit = 1LL << 22;   // drain waits: polls x 256 ns back-off, about one second
+constexpr long long kWaitCycles = 1LL << 31;  // pipeline waits: about one second of SM clock
 // INT8 work items span at most 2^15 samples: int32 register sums of |x| <= 128
 // products stay below 2^29, so masters and their 2x2 combine are exact.
 constexpr long kInt8ItemMax = 32768;
@@ -97,15 +98,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false on abort/timeout.
+// Bounded wait: true when the phase completed, false on abort/timeout.  It
+// polls try_wait (which suspends the thread in hardware until the phase
+// completes or a short time limit passes) without software sleeps, so a
+// waiter resumes as soon as its data lands; every 256 polls it checks the
+// CTA's abort flag and a clock-based limit of kWaitCycles (~1 s).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                           int *err, int code) {
-    for (long long it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (int it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (it >= 64) {
+        if ((it & 255) == 0) {
             if (*abort_flag) return false;
-            __nanosleep(256);
-            if (it > kWaitLimit) {
+            if (clock64() - t0 > kWaitCycles) {
                 *abort_flag = 1;
                 atomicCAS(err, 0, code);
                 return false;
@@ -125,6 +131,16 @@ __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, i
     asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y)
                  : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
 }
 
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -212,6 +228,76 @@ __device__ __forceinline__ bool decode_item(const TcParams &P, int item, Item &i
 // (32 MMAs, <= 2^-18 relative) for split FP16, 1024 samples (<= 2^-17) for
 // plain FP16, whose operand rounding (2^-11) dominates anyway.
 __device__ __forceinline__ int chunk_steps(int mode) { return mode == ACF_X_FP16 ? 16 : 8; }
+
+// Flush one epilogue thread's register sums of a finished tile: combine each
+// 2x2 real block into a complex visibility (in place: afterwards m[2k], m[2k+1]
+// hold Re, Im of V[i][jbase + k]) and write the lane's run of up to 32
+// consecutive visibilities of row i with 16-byte stores (or atomics).
+__device__ __forceinline__ void flush_tile(const JobDev &J, int p, int i, int jbase, int odd, bool exact,
+                                           uint32_t (&m)[128])
+{
+    // flush: combine 2x2 real blocks into complex visibilities, in place:
+    // after iteration k, m[2k], m[2k+1] hold (Re, Im) of V[i][jbase + k]
+    const long NB = (long)J.N * (J.N + 1) / 2;
+    const long prow = (long)p * NB + (long)i * (i + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t s0v = odd ? m[2 * k] : m[64 + 2 * k];
+        const uint32_t s1v = odd ? m[2 * k + 1] : m[65 + 2 * k];
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0v, 1);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, s1v, 1);
+        const uint32_t own0 = odd ? m[64 + 2 * k] : m[2 * k];
+        const uint32_t own1 = odd ? m[65 + 2 * k] : m[2 * k + 1];
+        // even lane: a = own0, b = own1, c = r0, d = r1; odd lane: c, d own, a, b received
+        const uint32_t a = odd ? r0 : own0, bq = odd ? r1 : own1;
+        const uint32_t c = odd ? own0 : r0, d = odd ? own1 : r1;
+        if (exact) {
+            // exact in int32: items span <= 32,768 samples, so |D| <= 128^2 * 2^15 = 2^29
+            m[2 * k] = (uint32_t)((int)a + (int)d);
+            m[2 * k + 1] = (uint32_t)((int)c - (int)bq);
+        } else {
+            m[2 * k] = __float_as_uint((__uint_as_float(a) + __uint_as_float(d)) * J.vscale);
+            m[2 * k + 1] = __float_as_uint((__uint_as_float(c) - __uint_as_float(bq)) * J.vscale);
+        }
+    }
+    // valid run of this lane: j in [jbase, min(jbase + 32, i + 1)), row i < N
+    const int nval = (i < J.N) ? max(0, min(32, i + 1 - jbase)) : 0;
+    if (nval > 0) {
+        if (exact) {
+            long long *dst = static_cast<long long *>(J.V) + 2 * (prow + jbase);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (k < nval) {
+                    const long long re = (int)m[2 * k], im = (int)m[2 * k + 1];
+                    if (J.store) {
+                        *reinterpret_cast<longlong2 *>(dst + 2 * k) = make_longlong2(re, im);
+                    } else {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k), (unsigned long long)re);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k + 1), (unsigned long long)im);
+                    }
+                }
+            }
+        } else {
+            float2 *dst = static_cast<float2 *>(J.V) + (prow + jbase);
+            // pair elements on 16-byte boundaries: a leading single when the run starts odd
+            const int lead = (int)((prow + jbase) & 1);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float2 v0 = make_float2(__uint_as_float(m[2 * k]), __uint_as_float(m[2 * k + 1]));
+                const bool single = (k == 0 && lead) || (k + 1 == nval && ((k - lead) & 1) == 0);
+                const bool pair_start = !single && ((k - lead) & 1) == 0 && k + 1 < nval;
+                if (k < nval && single) {
+                    if (J.store) dst[k] = v0;
+                    else atomicAdd(dst + k, v0);
+                } else if (k < 31 && k < nval && pair_start) {
+                    const float4 v = make_float4(v0.x, v0.y, __uint_as_float(m[2 * k + 2]), __uint_as_float(m[2 * k + 3]));
+                    if (J.store) *reinterpret_cast<float4 *>(dst + k) = v;
+                    else atomicAdd(reinterpret_cast<float4 *>(dst + k), v);
+                }
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant__ TcParams P)
 {
@@ -433,69 +519,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             }
             if (!ok) break;
             if (!active) continue;
-            // flush: combine 2x2 real blocks into complex visibilities, in place:
-            // after iteration k, m[2k], m[2k+1] hold (Re, Im) of V[i][jbase + k]
-            const int i = it.bi * 64 + 16 * q + (lane >> 1);
-            const int jbase = (J.nt * it.bj + 128 * half) / 2 + 32 * odd;
-            const long NB = (long)J.N * (J.N + 1) / 2;
-            const long prow = (long)it.p * NB + (long)i * (i + 1) / 2;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const uint32_t s0v = odd ? m[2 * k] : m[64 + 2 * k];
-                const uint32_t s1v = odd ? m[2 * k + 1] : m[65 + 2 * k];
-                const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0v, 1);
-                const uint32_t r1 = __shfl_xor_sync(0xffffffffu, s1v, 1);
-                const uint32_t own0 = odd ? m[64 + 2 * k] : m[2 * k];
-                const uint32_t own1 = odd ? m[65 + 2 * k] : m[2 * k + 1];
-                // even lane: a = own0, b = own1, c = r0, d = r1; odd lane: c, d own, a, b received
-                const uint32_t a = odd ? r0 : own0, bq = odd ? r1 : own1;
-                const uint32_t c = odd ? own0 : r0, d = odd ? own1 : r1;
-                if (exact) {
-                    // exact in int32: items span <= 32,768 samples, so |D| <= 128^2 * 2^15 = 2^29
-                    m[2 * k] = (uint32_t)((int)a + (int)d);
-                    m[2 * k + 1] = (uint32_t)((int)c - (int)bq);
-                } else {
-                    m[2 * k] = __float_as_uint((__uint_as_float(a) + __uint_as_float(d)) * J.vscale);
-                    m[2 * k + 1] = __float_as_uint((__uint_as_float(c) - __uint_as_float(bq)) * J.vscale);
-                }
-            }
-            // valid run of this lane: j in [jbase, min(jbase + 32, i + 1)), row i < N
-            const int nval = (i < J.N) ? max(0, min(32, i + 1 - jbase)) : 0;
-            if (nval > 0) {
-                if (exact) {
-                    long long *dst = static_cast<long long *>(J.V) + 2 * (prow + jbase);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        if (k < nval) {
-                            const long long re = (int)m[2 * k], im = (int)m[2 * k + 1];
-                            if (J.store) {
-                                *reinterpret_cast<longlong2 *>(dst + 2 * k) = make_longlong2(re, im);
-                            } else {
-                                atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k), (unsigned long long)re);
-                                atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * k + 1), (unsigned long long)im);
-                            }
-                        }
-                    }
-                } else {
-                    float2 *dst = static_cast<float2 *>(J.V) + (prow + jbase);
-                    // pair elements on 16-byte boundaries: a leading single when the run starts odd
-                    const int lead = (int)((prow + jbase) & 1);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const float2 v0 = make_float2(__uint_as_float(m[2 * k]), __uint_as_float(m[2 * k + 1]));
-                        const bool single = (k == 0 && lead) || (k + 1 == nval && ((k - lead) & 1) == 0);
-                        const bool pair_start = !single && ((k - lead) & 1) == 0 && k + 1 < nval;
-                        if (k < nval && single) {
-                            if (J.store) dst[k] = v0;
-                            else atomicAdd(dst + k, v0);
-                        } else if (k < 31 && k < nval && pair_start) {
-                            const float4 v = make_float4(v0.x, v0.y, __uint_as_float(m[2 * k + 2]), __uint_as_float(m[2 * k + 3]));
-                            if (J.store) *reinterpret_cast<float4 *>(dst + k) = v;
-                            else atomicAdd(reinterpret_cast<float4 *>(dst + k), v);
-                        }
-                    }
-                }
-            }
+            flush_tile(J, it.p, it.bi * 64 + 16 * q + (lane >> 1), (J.nt * it.bj + 128 * half) / 2 + 32 * odd, odd,
+                       exact, m);
 #pragma unroll
             for (int k = 0; k < 128; ++k) m[k] = 0u;
         }
@@ -506,6 +531,302 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two-SM variant: a cluster of two CTAs computes one 256x256 real tile with
+// tcgen05.mma.cta_group::2 (M = 256 split across the pair, N = 256 split in the
+// operand load).  Each CTA loads only its 128 A rows and its 128 B rows per K
+// step (32 KB instead of 48 KB), so six slots fit in shared memory and each SM
+// lands a third fewer operand bytes per MMA.  CTA rank 0 (the leader) issues
+// the MMAs; both CTAs' TMA loads complete on the leader's slot barrier, and the
+// leader's commits are multicast to both CTAs' slot and accumulator barriers.
+// Each CTA keeps two 256-column accumulators (its 128 rows of the tile) so the
+// epilogue drains one chunk while the next accumulates; epilogue warps of both
+// CTAs report a drained chunk to the leader.  The pair allocation is collective
+// (both CTAs receive the same TMEM base, which the kernel checks).
+// ---------------------------------------------------------------------------
+constexpr int kSlots2 = 6;
+constexpr int kSlotBytes2 = 32 * 1024;          // own 128 A rows + own 128 B rows
+constexpr uint32_t kTmemCols2 = 512;            // two 256-column accumulators per CTA
+constexpr int kBM2 = 256;                       // real rows per tile side
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Load into this CTA's shared memory, completing on the pair leader's barrier.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void mma_f16_pair(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"((uint16_t)0x3)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t idesc_f16_pair() {
+    // D fp32, A/B fp16, both K-major, N = 256, M = 256 (across the CTA pair)
+    return (1u << 4) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+// Square 256x256 tiles of the lower triangle, row-major in bi >= bj.
+__host__ __device__ inline int sq_tiles_per_problem(int N) {
+    const int nb = (2 * N + kBM2 - 1) / kBM2;
+    return nb * (nb + 1) / 2;
+}
+
+__device__ __forceinline__ bool decode_item2(const TcParams &P, int item, Item &it) {
+    int j = 0;
+    while (j + 1 < P.n_jobs && item >= P.jobs[j + 1].item_begin) ++j;
+    const JobDev &J = P.jobs[j];
+    int local = item - J.item_begin;
+    const int per_p = J.tiles_pp * J.k_split;
+    it.job = j;
+    it.p = local / per_p;
+    int rem = local - it.p * per_p;
+    int tile = rem / J.k_split;
+    const int s = rem - tile * J.k_split;
+    int bi = 0;
+    while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+    it.bi = bi;
+    it.bj = tile - bi * (bi + 1) / 2;
+    const long K64 = (J.n_time + 63) / 64 * 64;
+    const long per = ((K64 + J.k_split - 1) / J.k_split + 63) / 64 * 64;
+    it.k0 = (long)s * per;
+    it.k1 = min(K64, it.k0 + per);
+    return it.k0 < it.k1;
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constant__ TcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full_bar[kSlots2], empty_bar[kSlots2], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots2; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 2);      // leader's: one expect_tx from each CTA's producer
+            mbar_init(smem_u32(&empty_bar[s]), 1);     // the leader's multicast commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), 2 * kEpiWarps);  // leader's: every epilogue warp of both CTAs
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(kTmemCols2)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync();
+    const uint32_t tmem = tmem_base_s;
+    // the pair must see one accumulator address; otherwise record an error and do no work
+    if (threadIdx.x == 0) {
+        const uint32_t peer = ld_cluster_u32(mapa_u32(smem_u32(&tmem_base_s), rank ^ 1u));
+        if (peer != tmem) {
+            abort_flag = 1;
+            atomicCAS(P.err, 0, 9);
+        }
+    }
+    __syncthreads();
+    const bool run = !abort_flag;
+    cluster_sync();   // both CTAs decided before either starts
+    const uint32_t full_leader0 = mapa_u32(smem_u32(&full_bar[0]), 0);
+    const uint32_t acce_leader0 = mapa_u32(smem_u32(&acce_bar[0]), 0);
+
+    if (!run) {
+        // nothing issued: fall through to the common exit
+    } else if (warp == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        if (lane == 0) {
+            for (int j = 0; j < P.n_jobs; ++j)
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.maps[j][0])) : "memory");
+            long pos = 0;
+            bool ok = true;
+            for (int item = cid; item < P.n_items && ok; item += ncl) {
+                Item it;
+                if (!decode_item2(P, item, it)) continue;
+                const JobDev &J = P.jobs[it.job];
+                const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
+                const int rowA = it.p * 2 * J.N + it.bi * kBM2 + (int)rank * kBM;
+                const int rowB = it.p * 2 * J.N + it.bj * kBM2 + (int)rank * kBM;
+                for (long k = it.k0; k < it.k1 && ok; k += kBK) {
+                    for (int h = 0; h < spk && ok; ++h) {
+                        const int slot = (int)(pos % kSlots2);
+                        const uint32_t ph = (uint32_t)((pos / kSlots2) & 1);
+                        ok = mbar_wait(smem_u32(&empty_bar[slot]), ph ^ 1, &abort_flag, P.err, 11);
+                        if (!ok) break;
+                        const uint32_t fb = full_leader0 + (uint32_t)(slot * sizeof(uint64_t));
+                        mbar_expect_tx_cluster(fb, (uint32_t)kSlotBytes2);
+                        const uint32_t base = smem_u32(smem + slot * kSlotBytes2);
+                        const CUtensorMap *map = &P.maps[it.job][h];
+                        tma_load_2d_pair(base, map, fb, (int)k, rowA);
+                        tma_load_2d_pair(base + kBM * kBK * 2, map, fb, (int)k, rowB);
+                        ++pos;
+                    }
+                }
+            }
+            // before the CTA may exit: the leader's MMAs have consumed every fill
+            for (long q = pos - 1; q >= 0 && q >= pos - kSlots2; --q) {
+                const int slot = (int)(q % kSlots2);
+                for (long long it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&empty_bar[slot]), (uint32_t)((q / kSlots2) & 1)); ++it) {
+                    if (abort_flag) break;
+                    __nanosleep(256);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (leader only) ----------------
+        if (lane == 0 && leader) {
+            long pos = 0, cc = 0;
+            bool ok = true;
+            const uint32_t idesc = idesc_f16_pair();
+            for (int item = cid; item < P.n_items && ok; item += ncl) {
+                Item it;
+                if (!decode_item2(P, item, it)) continue;
+                const JobDev &J = P.jobs[it.job];
+                const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
+                const long steps = (it.k1 - it.k0) / kBK;
+                const long csteps = chunk_steps(J.mode);
+                for (long s0 = 0; s0 < steps && ok; s0 += csteps) {
+                    // accumulator b is free once both CTAs drained the chunk it last held
+                    const int b = (int)(cc & 1);
+                    ok = mbar_wait(smem_u32(&acce_bar[b]), (uint32_t)(((cc >> 1) & 1) ^ 1), &abort_flag, P.err, 12);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t dt = tmem + (uint32_t)(b * 256);
+                    const long s1 = min(steps, s0 + csteps);
+                    for (long s = s0; s < s1 && ok; ++s) {
+                        int slot[2];
+                        for (int h = 0; h < spk; ++h) {
+                            slot[h] = (int)(pos % kSlots2);
+                            const uint32_t ph = (uint32_t)((pos / kSlots2) & 1);
+                            ok = ok && mbar_wait(smem_u32(&full_bar[slot[h]]), ph, &abort_flag, P.err, 13);
+                            ++pos;
+                        }
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a_hi = smem_u32(smem + slot[0] * kSlotBytes2);
+                        const uint64_t dah = desc_sw128(a_hi), dbh = desc_sw128(a_hi + kBM * kBK * 2);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint32_t acc = (s > s0 || kk > 0) ? 1u : 0u;
+                            mma_f16_pair(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
+                            if (spk == 2) {
+                                const uint32_t a_lo = smem_u32(smem + slot[1] * kSlotBytes2);
+                                const uint64_t dal = desc_sw128(a_lo), dbl = desc_sw128(a_lo + kBM * kBK * 2);
+                                mma_f16_pair(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
+                                mma_f16_pair(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
+                            }
+                        }
+                        for (int h = 0; h < spk; ++h) mma_commit_pair(smem_u32(&empty_bar[slot[h]]));
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(smem_u32(&accf_bar[b]));
+                    ++cc;
+                }
+            }
+            mma_commit_pair(smem_u32(&done_bar));
+            for (long long it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&done_bar), 0); ++it) __nanosleep(256);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9, both CTAs) ----------------
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int odd = lane & 1;
+        uint32_t m[128];
+#pragma unroll
+        for (int k = 0; k < 128; ++k) m[k] = 0u;
+        long cc = 0;
+        bool ok = true;
+        for (int item = cid; item < P.n_items && ok; item += ncl) {
+            Item it;
+            if (!decode_item2(P, item, it)) continue;
+            const JobDev &J = P.jobs[it.job];
+            const bool exact = J.mode == ACF_X_INT8;
+            const long steps = (it.k1 - it.k0) / kBK;
+            const long csteps = chunk_steps(J.mode);
+            for (long s0 = 0; s0 < steps; s0 += csteps) {
+                const int b = (int)(cc & 1);
+                int w_ok = 0;
+                if (lane == 0) w_ok = mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)((cc >> 1) & 1), &abort_flag, P.err, 14);
+                ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 256 + half * 128);
+#pragma unroll
+                for (int piece = 0; piece < 4; ++piece) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + piece * 32, r);
+                    tmem_wait_ld();
+                    if (exact) {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            m[piece * 32 + k] = (uint32_t)((int)m[piece * 32 + k] + __float2int_rn(__uint_as_float(r[k])));
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            m[piece * 32 + k] = __float_as_uint(__uint_as_float(m[piece * 32 + k]) + __uint_as_float(r[k]));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acce_leader0 + (uint32_t)(b * sizeof(uint64_t)));
+                ++cc;
+            }
+            if (!ok) break;
+            // this CTA holds real rows [256 bi + 128 rank, +128) of the tile
+            flush_tile(J, it.p, it.bi * 128 + 64 * (int)rank + 16 * q + (lane >> 1), it.bj * 128 + 64 * half + 32 * odd,
+                       odd, exact, m);
+#pragma unroll
+            for (int k = 0; k < 128; ++k) m[k] = 0u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols2) : "memory");
     }
 }
 
@@ -529,6 +850,7 @@ struct TcPlan {
     int slot_of[kMaxJobs];   // caller's job index -> position in the work list
     int grid = 0;
     size_t smem = 0;
+    bool pair = false;       // two-SM kernel (CTA pairs, cta_group::2)
 };
 
 bool tc_supported(int device)
@@ -574,14 +896,14 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
         D.N = J.N;
         D.n_problems = J.n_problems;
         D.mode = J.mode;
-        D.nt = (tun.n_tile == 128) ? 128 : 256;
+        D.nt = (tun.n_tile == 128 && !tun.pair) ? 128 : 256;
         D.n_time = J.n_time;
         const long K64 = round_up(J.n_time, 64);
         int ks = std::max(1, tun.k_split);
         if (J.mode == ACF_X_INT8) ks = std::max<long>(ks, (K64 + kInt8ItemMax - 1) / kInt8ItemMax);
         D.k_split = ks;
         D.mb = (2 * J.N + kBM - 1) / kBM;
-        D.tiles_pp = tiles_per_problem(J.N, D.nt);
+        D.tiles_pp = tun.pair ? sq_tiles_per_problem(J.N) : tiles_per_problem(J.N, D.nt);
         D.item_begin = items;
         D.vscale = J.vscale;
         D.store = (J.store && ks == 1) ? 1 : 0;
@@ -605,17 +927,40 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
     }
     p->params.n_jobs = n_jobs;
     p->params.n_items = items;
+    p->pair = tun.pair != 0;
     p->params.err = device_error_word();
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    p->grid = std::max(1, std::min(items, sms));
     p->smem = (size_t)kSlots * kSlotBytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    static_assert(kSlots * kSlotBytes == kSlots2 * kSlotBytes2, "both kernels use the same shared memory");
+    cudaError_t e = cudaFuncSetAttribute(p->pair ? k_xeng_tc2 : k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p->smem);
     if (e != cudaSuccess) {
         delete p;
         if (err) *err = "cudaFuncSetAttribute(max dynamic smem) failed";
         return e;
+    }
+    if (!p->pair) {
+        p->grid = std::max(1, std::min(items, sms));
+    } else {
+        // CTA pairs must be co-resident: as many as fit at once, at most one per work item
+        int clusters = sms / 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * clusters);
+        cfg.blockDim = dim3(kThreadsTc);
+        cfg.dynamicSmemBytes = p->smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_xeng_tc2, &cfg) == cudaSuccess && n > 0) clusters = std::min(clusters, n);
+        cudaGetLastError();
+        p->grid = 2 * std::max(1, std::min(items, clusters));
     }
     *out = p;
     return cudaSuccess;
@@ -642,9 +987,26 @@ int tc_plan_job_split(const TcPlan *p, int job) { return p->params.jobs[p->slot_
 cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
 {
     if (p->params.n_items == 0) return cudaSuccess;
-    k_xeng_tc<<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
+    if (!p->pair) {
+        k_xeng_tc<<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
+        g_launches++;
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p->grid);
+    cfg.blockDim = dim3(kThreadsTc);
+    cfg.dynamicSmemBytes = p->smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_xeng_tc2, p->params);
     g_launches++;
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int tc_plan_items(const TcPlan *p) { return p->params.n_items; }
