@@ -19,13 +19,14 @@
 //   warps 2-9  epilogue: tcgen05.ld the finished accumulator chunk, fold it
 //              into per-thread register masters (fp32, or int32 for the exact
 //              mode), and at the end of a work item combine the 2x2 blocks
-//              and atomically add the visibilities into the packed triangle.
+//              and store (or, when a tile has several writers, atomically
+//              add) the visibilities into the packed triangle.
 // Modes: FP16 (one product per K step), FP16x3 (hi*hi + hi*lo + lo*hi, the
 // lo operands in a second slot), INT8 (fp16 holding integers |x| <= 127:
 // products are exact and each 512-sample chunk sum stays below 2^24, so the
 // fp32 tensor-core accumulation is exact; chunks are folded into int32
-// masters and work items never exceed 65,536 samples, so the masters cannot
-// overflow; the final combine is in int64).
+// masters and work items never exceed 32,768 samples, so the masters stay
+// below 2^29 and their 2x2 combine below 2^31; the output is int64).
 // Every mbarrier wait is bounded; on timeout the CTA records an error word,
 // drains its own TMA copies and MMAs, frees TMEM and returns.
 #include <cudaTypedefs.h>
@@ -42,6 +43,8 @@ namespace {
 constexpr int kMaxJobs = 64;
 constexpr int kSlots = 4;
 constexpr int kSlotBytes = 48 * 1024;          // A 16 KB + B up to 32 KB
+constexpr int kSlots2 = 6;                      // two-SM kernel: ring slots per CTA
+constexpr int kSlotBytes2 = 32 * 1024;          // own 128 A rows + own 128 B rows
 constexpr int kBM = 128, kBK = 64;
 constexpr int kThreadsTc = 320;
 constexpr int kEpiWarps = 8;
@@ -51,7 +54,6 @@ constexpr long long kWaitCycles = 1LL << 31;  // pipeline waits: about one secon
 // INT8 work items span at most 2^15 samples: int32 register sums of |x| <= 128
 // products stay below 2^29, so masters and their 2x2 combine are exact.
 constexpr long kInt8ItemMax = 32768;
-constexpr int kPfSteps = 12;                  // L2 prefetch distance in K steps
 
 struct JobDev {
     void *V;
@@ -127,12 +129,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y)
-                 : "memory");
-}
-
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -166,6 +162,17 @@ __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, 
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mma_f16_pair(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"((uint16_t)0x3)
+                 : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -228,6 +235,64 @@ __device__ __forceinline__ bool decode_item(const TcParams &P, int item, Item &i
 // (32 MMAs, <= 2^-18 relative) for split FP16, 1024 samples (<= 2^-17) for
 // plain FP16, whose operand rounding (2^-11) dominates anyway.
 __device__ __forceinline__ int chunk_steps(int mode) { return mode == ACF_X_FP16 ? 16 : 8; }
+// ---------------------------------------------------------------------------
+// MMA issue for the K steps [s0, s1) of one accumulator chunk.  SPK is the
+// number of ring slots per K step (1: one fp16 operand; 2: split FP16 hi and
+// lo, issuing hi*hi, hi*lo and lo*hi).  The count is a template parameter so
+// that the slot indices stay in registers and the unrolled issue sequence has
+// no branches: a runtime count with the split-FP16 MMAs behind a branch inside
+// the K loop ran the whole X-engine ~1.7x slower in FP16 mode.  PAIR selects
+// the two-SM form (cta_group::2 MMAs and multicast commits, issued by the
+// leader CTA).  Returns false when a wait gave up (abort or timeout).
+template <int SPK, bool PAIR>
+__device__ __forceinline__ bool issue_steps(uint32_t ring, uint64_t *full_bar, uint64_t *empty_bar, long &pos, long s0,
+                                            long s1, uint32_t dt, uint32_t idesc, volatile int *abort_flag, int *err)
+{
+    constexpr int kRing = PAIR ? kSlots2 : kSlots;
+    constexpr uint32_t kStride = PAIR ? kSlotBytes2 : kSlotBytes;
+    for (long s = s0; s < s1; ++s) {
+        int slot[SPK];
+#pragma unroll
+        for (int h = 0; h < SPK; ++h) {
+            slot[h] = (int)(pos % kRing);
+            if (!mbar_wait(smem_u32(&full_bar[slot[h]]), (uint32_t)((pos / kRing) & 1), abort_flag, err, PAIR ? 13 : 3))
+                return false;
+            ++pos;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = ring + (uint32_t)slot[0] * kStride;
+        const uint64_t dah = desc_sw128(a_hi), dbh = desc_sw128(a_hi + kBM * kBK * 2);
+        uint64_t dal = 0, dbl = 0;
+        if constexpr (SPK == 2) {
+            const uint32_t a_lo = ring + (uint32_t)slot[1] * kStride;
+            dal = desc_sw128(a_lo);
+            dbl = desc_sw128(a_lo + kBM * kBK * 2);
+        }
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t acc = (s > s0 || kk > 0) ? 1u : 0u;
+            if constexpr (PAIR) {
+                mma_f16_pair(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
+                if constexpr (SPK == 2) {
+                    mma_f16_pair(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
+                    mma_f16_pair(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
+                }
+            } else {
+                mma_f16(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
+                if constexpr (SPK == 2) {
+                    mma_f16(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
+                    mma_f16(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < SPK; ++h) {
+            if constexpr (PAIR) mma_commit_pair(smem_u32(&empty_bar[slot[h]]));
+            else mma_commit(smem_u32(&empty_bar[slot[h]]));
+        }
+    }
+    return true;
+}
 
 // Flush one epilogue thread's register sums of a finished tile: combine each
 // 2x2 real block into a complex visibility (in place: afterwards m[2k], m[2k+1]
@@ -343,40 +408,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             }
             long pos = 0;
             bool ok = true;
-            // L2 prefetch cursor: kPfSteps K steps ahead of the loads, running on into
-            // this CTA's next work item, so first touches of X come from L2, not DRAM
-            int pf_item = blockIdx.x;
-            Item pf;
-            bool pf_ok = false;
-            long pf_k = 0;
-            auto pf_seek = [&]() {
-                while (pf_item < P.n_items) {
-                    if (decode_item(P, pf_item, pf)) {
-                        pf_ok = true;
-                        pf_k = pf.k0;
-                        return;
-                    }
-                    pf_item += gridDim.x;
-                }
-                pf_ok = false;
-            };
-            auto pf_step = [&]() {
-                if (!pf_ok) return;
-                const JobDev &Jp = P.jobs[pf.job];
-                const int rA = pf.p * 2 * Jp.N + pf.bi * kBM, rB = pf.p * 2 * Jp.N + pf.bj * Jp.nt;
-                for (int h = 0; h < (Jp.mode == ACF_X_FP16x3 ? 2 : 1); ++h) {
-                    const CUtensorMap *mp = &P.maps[pf.job][h];
-                    tma_prefetch_2d(mp, (int)pf_k, rA);
-                    for (int q = 0; q < Jp.nt / kBM; ++q) tma_prefetch_2d(mp, (int)pf_k, rB + q * kBM);
-                }
-                pf_k += kBK;
-                if (pf_k >= pf.k1) {
-                    pf_item += gridDim.x;
-                    pf_seek();
-                }
-            };
-            pf_seek();
-            for (int s = 0; s < kPfSteps; ++s) pf_step();
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
                 Item it;
                 if (!decode_item(P, item, it)) continue;
@@ -386,7 +417,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
                 const int rowB = it.p * 2 * J.N + it.bj * J.nt;
                 const uint32_t bytes = (uint32_t)(kBM + J.nt) * kBK * 2;
                 for (long k = it.k0; k < it.k1 && ok; k += kBK) {
-                    pf_step();
                     for (int h = 0; h < spk && ok; ++h) {
                         const int slot = (int)(pos % kSlots);
                         const uint32_t ph = (uint32_t)((pos / kSlots) & 1);
@@ -423,6 +453,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
                 const JobDev &J = P.jobs[it.job];
                 const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
                 const uint32_t idesc = idesc_f16(J.nt);
+                const uint32_t ring = smem_u32(smem);
                 const long steps = (it.k1 - it.k0) / kBK;
                 const long csteps = chunk_steps(J.mode);
                 for (long s0 = 0; s0 < steps && ok; s0 += csteps) {
@@ -432,33 +463,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(b * 256);
                     const long s1 = min(steps, s0 + csteps);
-                    for (long s = s0; s < s1 && ok; ++s) {
-                        int slot[2];
-                        for (int h = 0; h < spk; ++h) {
-                            slot[h] = (int)(pos % kSlots);
-                            const uint32_t ph = (uint32_t)((pos / kSlots) & 1);
-                            ok = ok && mbar_wait(smem_u32(&full_bar[slot[h]]), ph, &abort_flag, P.err, 3);
-                            ++pos;
-                        }
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t a_hi = smem_u32(smem + slot[0] * kSlotBytes);
-                        const uint32_t b_hi = a_hi + kBM * kBK * 2;
-                        const uint64_t dah = desc_sw128(a_hi), dbh = desc_sw128(b_hi);
-#pragma unroll
-                        for (int kk = 0; kk < kBK / 16; ++kk) {
-                            const uint32_t acc = (s > s0 || kk > 0) ? 1u : 0u;
-                            mma_f16(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
-                            if (spk == 2) {
-                                const uint32_t a_lo = smem_u32(smem + slot[1] * kSlotBytes);
-                                const uint32_t b_lo = a_lo + kBM * kBK * 2;
-                                const uint64_t dal = desc_sw128(a_lo), dbl = desc_sw128(b_lo);
-                                mma_f16(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
-                                mma_f16(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
-                            }
-                        }
-                        for (int h = 0; h < spk; ++h) mma_commit(smem_u32(&empty_bar[slot[h]]));
-                    }
+                    ok = spk == 2 ? issue_steps<2, false>(ring, full_bar, empty_bar, pos, s0, s1, dt, idesc, &abort_flag, P.err)
+                                  : issue_steps<1, false>(ring, full_bar, empty_bar, pos, s0, s1, dt, idesc, &abort_flag, P.err);
                     if (!ok) break;
                     mma_commit(smem_u32(&accf_bar[b]));
                     ++cc;
@@ -547,8 +553,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
 // CTAs report a drained chunk to the leader.  The pair allocation is collective
 // (both CTAs receive the same TMEM base, which the kernel checks).
 // ---------------------------------------------------------------------------
-constexpr int kSlots2 = 6;
-constexpr int kSlotBytes2 = 32 * 1024;          // own 128 A rows + own 128 B rows
 constexpr uint32_t kTmemCols2 = 512;            // two 256-column accumulators per CTA
 constexpr int kBM2 = 256;                       // real rows per tile side
 
@@ -575,17 +579,6 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
         "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
         : "memory");
-}
-__device__ __forceinline__ void mma_f16_pair(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"((uint16_t)0x3)
-                 : "memory");
 }
 __device__ __forceinline__ uint32_t idesc_f16_pair() {
     // D fp32, A/B fp16, both K-major, N = 256, M = 256 (across the CTA pair)
@@ -719,6 +712,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
             long pos = 0, cc = 0;
             bool ok = true;
             const uint32_t idesc = idesc_f16_pair();
+            const uint32_t ring = smem_u32(smem);
             for (int item = cid; item < P.n_items && ok; item += ncl) {
                 Item it;
                 if (!decode_item2(P, item, it)) continue;
@@ -734,31 +728,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(b * 256);
                     const long s1 = min(steps, s0 + csteps);
-                    for (long s = s0; s < s1 && ok; ++s) {
-                        int slot[2];
-                        for (int h = 0; h < spk; ++h) {
-                            slot[h] = (int)(pos % kSlots2);
-                            const uint32_t ph = (uint32_t)((pos / kSlots2) & 1);
-                            ok = ok && mbar_wait(smem_u32(&full_bar[slot[h]]), ph, &abort_flag, P.err, 13);
-                            ++pos;
-                        }
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t a_hi = smem_u32(smem + slot[0] * kSlotBytes2);
-                        const uint64_t dah = desc_sw128(a_hi), dbh = desc_sw128(a_hi + kBM * kBK * 2);
-#pragma unroll
-                        for (int kk = 0; kk < kBK / 16; ++kk) {
-                            const uint32_t acc = (s > s0 || kk > 0) ? 1u : 0u;
-                            mma_f16_pair(dt, dah + 2 * kk, dbh + 2 * kk, idesc, acc);
-                            if (spk == 2) {
-                                const uint32_t a_lo = smem_u32(smem + slot[1] * kSlotBytes2);
-                                const uint64_t dal = desc_sw128(a_lo), dbl = desc_sw128(a_lo + kBM * kBK * 2);
-                                mma_f16_pair(dt, dah + 2 * kk, dbl + 2 * kk, idesc, 1u);
-                                mma_f16_pair(dt, dal + 2 * kk, dbh + 2 * kk, idesc, 1u);
-                            }
-                        }
-                        for (int h = 0; h < spk; ++h) mma_commit_pair(smem_u32(&empty_bar[slot[h]]));
-                    }
+                    ok = spk == 2 ? issue_steps<2, true>(ring, full_bar, empty_bar, pos, s0, s1, dt, idesc, &abort_flag, P.err)
+                                  : issue_steps<1, true>(ring, full_bar, empty_bar, pos, s0, s1, dt, idesc, &abort_flag, P.err);
                     if (!ok) break;
                     mma_commit_pair(smem_u32(&accf_bar[b]));
                     ++cc;
