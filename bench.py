@@ -54,7 +54,7 @@ def xeng_traffic_per_subband():
         txt = open(prof).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         m = re.search(r"xeng_tc.cu sha256 prefix `([0-9a-f]+)`", txt)
-        t = re.search(r"traffic_per_subband_bytes k_xeng_tc: (\d+)", txt)
+        t = re.search(r"traffic_per_subband_bytes k_xeng_tc2?: (\d+)", txt)
         if m and t and m.group(1) == h:
             return int(t.group(1))
     except OSError:
@@ -347,7 +347,7 @@ def main():
     tps = xeng_traffic_per_subband()
     roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16_sus"], unit="TFLOP/s",
                 frac=achieved / pk["bf16_sus"], traffic=None if tps is None else tps * n_sb,
-                note="X-engine (k_xeng_tc, FP16 operands, fp32 accumulation); algorithmic ops "
+                note="X-engine (k_xeng_tc2: SM pairs per 256x256 tile, FP16 operands, fp32 accumulation); algorithmic ops "
                      "8*N(N+1)/2*spectra*channels*subbands = %.3e per launch over its CUDA-event time %.3f ms; "
                      "peak = %s bf16 sustained (fp16 dense = bf16 dense on B300); frac of burst %.3f"
                      % (main_r["ops_per_step"], xeng_ms, pk["src"], achieved / pk["bf16"]))

@@ -143,8 +143,10 @@ acf_status acf_last_timing(acf_ctx *ctx, float *chan_ms, float *xeng_ms);
 
 /* Tensor-core X-engine variant for this context: 0 = one SM per 128x256 tile,
  * 1 = SM pairs (clusters of two CTAs) per 256x256 tile, each SM loading half
- * of both operands.  Rebuilds the launch plan; only between integrations.
- * EINVAL for other values, ESTATE mid-integration or in FP32 mode. */
+ * of both operands.  acf_create picks 1 in the FP16 modes with 512 or more
+ * inputs, else 0.
+ * Rebuilds the launch plan; only between integrations.  EINVAL for other
+ * values, ESTATE mid-integration or in FP32 mode. */
 acf_status acf_set_xengine_variant(acf_ctx *ctx, int variant);
 
 /* Release every resource.  Synchronises the device first.  NULL is a no-op. */

@@ -67,7 +67,7 @@ struct acf_ctx {
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> ev_copied;
     TcPlan *plan = nullptr;
-    int variant = 0;              // one SM per tile (measured faster than SM pairs)
+    int variant = 0;              // 0: one SM per 128x256 tile; 1: SM pairs per 256x256 tile
     int pushes = 0;
     bool ready = false;
     bool v_valid = false;         // V already holds this integration's partial sums
@@ -242,6 +242,11 @@ acf_status acf_create(acf_ctx **out, int n_inputs, int n_subbands, int n_channel
         return fail(nullptr, ACF_EUNSUPPORTED, "tensor-core modes need an sm_103 device");
     acf_ctx *c = new acf_ctx();
     c->N = n_inputs;
+    // SM pairs move a third fewer operand bytes per MMA; their 256x256 tiles
+    // pay off once the array fills several of them (FP16 and split FP16 on
+    // 1152 inputs: 11-14% faster per subband than one SM per tile).  The INT8
+    // path (576-input raw subbands) measured faster on one SM per tile.
+    c->variant = (n_inputs >= 512 && (mode == ACF_X_FP16 || mode == ACF_X_FP16x3)) ? 1 : 0;
     c->n_sb = n_subbands;
     c->C = n_channels;
     c->P = n_taps;

@@ -566,10 +566,6 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr) {
     asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
     return v;
 }
-__device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -628,7 +624,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots2; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), 2);      // leader's: one expect_tx from each CTA's producer
+            mbar_init(smem_u32(&full_bar[s]), 1);      // leader's: its producer's expect_tx for both CTAs' bytes
             mbar_init(smem_u32(&empty_bar[s]), 1);     // the leader's multicast commit
         }
         for (int b = 0; b < 2; ++b) {
@@ -688,7 +684,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
                         ok = mbar_wait(smem_u32(&empty_bar[slot]), ph ^ 1, &abort_flag, P.err, 11);
                         if (!ok) break;
                         const uint32_t fb = full_leader0 + (uint32_t)(slot * sizeof(uint64_t));
-                        mbar_expect_tx_cluster(fb, (uint32_t)kSlotBytes2);
+                        // Only the leader arrives, locally, expecting both CTAs' bytes; the
+                        // peer's copies just complete their bytes on the leader's barrier (a
+                        // transaction count may run ahead of its expect_tx).  A remote
+                        // release-cluster arrive per slot from the peer was slow enough to
+                        // starve the MMA.
+                        if (leader) mbar_expect_tx(smem_u32(&full_bar[slot]), 2u * (uint32_t)kSlotBytes2);
                         const uint32_t base = smem_u32(smem + slot * kSlotBytes2);
                         const CUtensorMap *map = &P.maps[it.job][h];
                         tma_load_2d_pair(base, map, fb, (int)k, rowA);
