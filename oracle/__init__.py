@@ -8,6 +8,9 @@ the paper's step order: FIR -> DFT -> bandpass -> transpose -> pair sums).
 This module only marshals numpy arrays into it and strings the steps
 together for whole streams.  It shares no code with the CUDA library.
 
+The post-correlation steps (delay compensation, channel integration,
+lost-sample weights, sigma-clip flagging) are plain numpy in ``post.py``.
+
 Every function here has a pin in ``tests/test_oracle_*.py``; none is
 "parity unpinned".
 """

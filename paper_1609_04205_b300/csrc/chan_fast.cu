@@ -309,24 +309,46 @@ struct Geo64 {
     static constexpr int VEC = VB / E, VPR = NI / VEC, ROWS = kMB * C, NV = ROWS * VPR;
     static constexpr int VPT = NV / NT;
     static constexpr int ROWI = ROWS + 4;
-    static constexpr int YROW = C + 1;                       // complex per spectrum row (y buffer)
-    static constexpr int OROW = OUTK == OUT_F32 ? C + 1 : C + 2;   // output row: float2 or half2 units
-    static constexpr int OUNIT = OUTK == OUT_F32 ? 8 : 4;
-    static constexpr int NOUT = OUTK == OUT_F16X3 ? 2 : 1;
+    // y rows: 64 complex + 8 of padding, so consecutive spectra start 8 bank
+    // pairs apart; columns are XOR-swizzled by (spectrum & 7) in their low three
+    // bits.  With the thread maps below, the FIR stores and both FFT passes touch
+    // 16 distinct 8-byte bank pairs per half-warp.
+    static constexpr int YS = C + 8;
+    static constexpr int OE = OUTK == OUT_F32 ? 4 : 2;       // output element bytes
+    static constexpr int NOUT = OUTK == OUT_F16X3 ? 2 : 1;   // output planes
     static constexpr int NROW = NI * C * 2;                  // output rows (input, channel, re|im)
-    static constexpr int SPT = NROW * (kMB / 8) * NOUT / NT; // 16-byte stores per thread per batch
-    static constexpr size_t SIN = (size_t)NI * ROWI * E;
-    static constexpr size_t SY = (size_t)NI * kMB * YROW * 8;
-    static constexpr size_t SOUT = (size_t)NI * kMB * OROW * OUNIT;
-    static constexpr size_t STW = C * 8 + C * 4;             // twiddles + bandpass*scale
+    // staging row: the batch's 16 spectra of one output row, time-contiguous,
+    // padded so the paired 32-bit stores and the 16-byte reads are conflict-free
+    static constexpr int ORB = OUTK == OUT_F32 ? 96 : 48;
+    static constexpr int PIECES = kMB * OE / 16;             // 16-byte pieces per row per batch
+    static constexpr int SPT = NROW * PIECES * NOUT / NT;    // 16-byte stores per thread per batch
+    static constexpr size_t SIN = ((size_t)NI * ROWI * E + 15) / 16 * 16;
+    static constexpr size_t SY = (size_t)NI * kMB * YS * 8;
+    static constexpr size_t SOUT = (size_t)NROW * ORB;
+    static constexpr size_t STW = C * 8 + C * 4;              // twiddles + bandpass x scale
     static constexpr size_t SMEM = SIN + SY + SOUT * NOUT + STW;
-    static_assert(NV % NT == 0 && (NROW * (kMB / 8) * NOUT) % NT == 0, "work must split evenly");
+    static_assert(NV % NT == 0 && (NROW * PIECES * NOUT) % NT == 0, "work must split evenly");
 };
 
 template <int VB> struct VecT;
 template <> struct VecT<16> { using T = uint4; };
 template <> struct VecT<8> { using T = uint2; };
 
+// 64-channel channeliser.  Per batch of 16 spectra:
+//   deposit   the batch's input rows (fetched one batch ahead into registers)
+//             are transposed into one shared-memory row per input;
+//   FIR       thread (input, phase q) slides its 16-tap window along the
+//             batch: y[mm][q] for 16 spectra;
+//   pass 1    thread (input, column s = q / 8) takes spectra q % 8 and q % 8 + 8:
+//             8-point DFT over y[s + 8r], times W_64^(s k1) (twiddles held in
+//             registers, fixed per thread), back to slot s + 8 k1;
+//   pass 2    thread (input, k1 = q / 8), same two spectra: 8-point DFT over
+//             slots 8 k1 + s gives channels c = k1 + 8 k2; bandpass x scale
+//             (registers, fixed per thread); neighbouring lanes hold
+//             consecutive spectra and swap one value per channel so that each
+//             writes a time-contiguous pair of one output row (real or
+//             imaginary part) to the staging buffer;
+//   store     16-byte pieces of 8 spectra per output row go to global memory.
 template <typename IN, int OUTK>
 __global__ void __launch_bounds__(256, 2)
 k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, long n_samples, int N,
@@ -346,7 +368,7 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
     const int tid = threadIdx.x;
     const int il = tid >> 6;               // local input (two warps each)
     static_assert(NT == NI * 64, "one thread per (input, phase)");
-    const int q = tid & 63;                // channel phase (FIR) / work index (FFT passes)
+    const int q = tid & 63;                // channel phase (FIR); FFT column / channel group (passes)
     const int n0 = blockIdx.x * NI;
     const int sb = blockIdx.z;
     const long T64 = (T + 63) / 64 * 64;
@@ -355,17 +377,19 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
     const long stream_len = n_hist + n_samples;
     const IN *hsb = hist ? hist + (long)sb * n_hist * N : nullptr;
     const IN *isb = in + (long)sb * n_samples * N;
-    float2 *yw = ybuf + (size_t)il * kMB * G::YROW;          // this input's y rows
+    float2 *yw = ybuf + (size_t)il * kMB * G::YS;            // this input's y rows
 
-    if (tid < C) {
-        stw[tid] = tw_g[tid];
-        sbp[tid] = __ldg(bp + tid) * (OUTK == OUT_F32 ? 1.f : scale);
-    }
     float2 hr[kP];              // (h, h): one packed fp32x2 FMA per tap updates (re, im)
 #pragma unroll
     for (int k = 0; k < kP; ++k) {
         const float hv = __ldg(h + k * C + q);
         hr[k] = make_float2(hv, hv);
+    }
+    const int sw = q & 7;       // column swizzle of this thread's spectra (mm & 7)
+    const int grp = q >> 3;     // pass-1 column s, pass-2 channel group k1
+    if (tid < C) {             // read after the first barrier
+        stw[tid] = tw_g[tid];
+        sbp[tid] = __ldg(bp + tid) * (OUTK == OUT_F32 ? 1.f : scale);
     }
 
     using V = typename VecT<G::VB>::T;
@@ -402,25 +426,6 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
             for (int k = 0; k < G::VEC; ++k) sin[(vc * G::VEC + k) * G::ROWI + row] = vals[k];
         }
     };
-    // per-thread store slots, identical for every batch: global element offset (without the
-    // batch's first spectrum), shared-memory offset, 8-spectrum group, plane, validity
-    long st_goff[G::SPT];
-    int st_soff[G::SPT];
-    unsigned st_meta = 0;     // bit v: valid; bit 8+v: group; bit 16+v: plane
-#pragma unroll
-    for (int v = 0; v < G::SPT; ++v) {
-        const int e = tid + v * NT;
-        const int plane = e / (G::NROW * 2);
-        const int rem = e % (G::NROW * 2);
-        const int row = rem % G::NROW, g = rem / G::NROW;
-        const int comp = row & 1, c = (row >> 1) % C, li = row / (2 * C);
-        const int nn = n0 + li;
-        st_meta |= (nn < N ? 1u : 0u) << v;
-        st_meta |= (unsigned)g << (8 + v);
-        st_meta |= (unsigned)plane << (16 + v);
-        st_goff[v] = (((long)sb * C + c) * (2L * N) + 2L * nn + comp) * t_stride + g * 8;
-        st_soff[v] = (int)(((size_t)(li * kMB + g * 8) * G::OROW + c) * 2 + comp);
-    }
 
     float2 win[kP];
     fetch(m_lo, kP - 1);
@@ -445,79 +450,84 @@ k_chan64(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, lo
                 a0 = __ffma2_rn(hr[k], win[(mm + k) % kP], a0);
                 a1 = __ffma2_rn(hr[k + 1], win[(mm + k + 1) % kP], a1);
             }
-            yw[mm * G::YROW + q] = __fadd2_rn(a0, a1);
+            yw[mm * G::YS + (q ^ (mm & 7))] = __fadd2_rn(a0, a1);
         }
         __syncthreads();
-        // pass 1: thread -> (mm = idx % 16, s = idx / 16), idx = q + 64 j
+        // pass 1: column s = grp of spectra sw and sw + 8
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int idx = q + 64 * j;
-            const int mm = idx & 15, sx = idx >> 4;
+            float2 *row = yw + (sw + 8 * j) * G::YS + (grp ^ sw);
             float2 a[8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) a[r] = yw[mm * G::YROW + sx + 8 * r];
+            for (int r = 0; r < 8; ++r) a[r] = row[8 * r];
             dft8(a);
 #pragma unroll
-            for (int k1 = 1; k1 < 8; ++k1) a[k1] = cmul(a[k1], stw[(sx * k1) & 63]);
+            for (int k1 = 1; k1 < 8; ++k1) a[k1] = cmul(a[k1], stw[(grp * k1) & 63]);
 #pragma unroll
-            for (int k1 = 0; k1 < 8; ++k1) yw[mm * G::YROW + sx + 8 * k1] = a[k1];
+            for (int k1 = 0; k1 < 8; ++k1) row[8 * k1] = a[k1];
         }
         __syncthreads();
-        // pass 2: thread -> (mm = idx % 16, k1 = idx / 16); channel c = k1 + 8 k2
+        // pass 2: channels grp + 8 k2 of spectra sw and sw + 8
+        const int odd = q & 1;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int idx = q + 64 * j;
-            const int mm = idx & 15, k1 = idx >> 4;
+            const int mm = sw + 8 * j;
+            const float2 *row = yw + mm * G::YS + 8 * grp;
             float2 a[8];
 #pragma unroll
-            for (int sx = 0; sx < 8; ++sx) a[sx] = yw[mm * G::YROW + 8 * k1 + sx];
+            for (int sx = 0; sx < 8; ++sx) a[sx] = row[sx ^ sw];
             dft8(a);
-            const size_t orow = (size_t)(il * kMB + mm) * G::OROW;
+            const bool live = m0 + mm < T;          // spectra past T are written as zeros
+            const int pcol = mm >> 1;               // pair of spectra (mm & ~1, mm | 1)
 #pragma unroll
             for (int k2 = 0; k2 < 8; ++k2) {
-                const int c = k1 + 8 * k2;
-                const float wc = sbp[c];
-                const float2 v = __fmul2_rn(a[k2], make_float2(wc, wc));
-                const float re = v.x, im = v.y;
+                const float wc = sbp[grp + 8 * k2];
+                float2 v = __fmul2_rn(a[k2], make_float2(wc, wc));
+                if (!live) v = make_float2(0.f, 0.f);
+                // even lane keeps Re of both spectra, odd lane Im of both
+                const float recv = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
+                const float first = odd ? recv : v.x, second = odd ? v.y : recv;
+                const int orow = il * 2 * C + 2 * (grp + 8 * k2) + odd;
                 if (OUTK == OUT_F32) {
-                    reinterpret_cast<float2 *>(sout)[orow + c] = make_float2(re, im);
+                    *reinterpret_cast<float2 *>(sout + (size_t)orow * G::ORB + 8 * pcol) = make_float2(first, second);
                 } else {
-                    const __half2 hv = __floats2half2_rn(re, im);
-                    reinterpret_cast<__half2 *>(sout)[orow + c] = hv;
+                    const __half2 hv = __floats2half2_rn(first, second);
+                    *reinterpret_cast<__half2 *>(sout + (size_t)orow * G::ORB + 4 * pcol) = hv;
                     if (OUTK == OUT_F16X3) {
                         const float2 f = __half22float2(hv);
-                        reinterpret_cast<__half2 *>(sout + G::SOUT)[orow + c] = __floats2half2_rn(re - f.x, im - f.y);
+                        *reinterpret_cast<__half2 *>(sout + G::SOUT + (size_t)orow * G::ORB + 4 * pcol) =
+                            __floats2half2_rn(first - f.x, second - f.y);
                     }
                 }
             }
         }
         __syncthreads();
-        // store: 16-byte pieces of 8 consecutive spectra
-#pragma unroll
+        // store: 16-byte pieces; a quarter-warp reads one piece of 8 rows
+        // (conflict-free staging reads), a warp writes whole 32-byte sectors.
+        // Not unrolled: at the 128-register cap an unrolled store loop made
+        // ptxas spill, and the spill reloads cost ~50% of the kernel time.
+#pragma unroll 1
         for (int v = 0; v < G::SPT; ++v) {
-            if (!((st_meta >> v) & 1u)) continue;
-            const int g = (st_meta >> (8 + v)) & 1u;
-            const int plane = (st_meta >> (16 + v)) & 1u;
-            const long m = m0 + g * 8;
-            const long gofs = st_goff[v] + m0;
-            if (OUTK == OUT_F32) {
-                const float *so = reinterpret_cast<const float *>(sout) + st_soff[v];
-                float vv[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) vv[k] = (m + k < T) ? so[k * G::OROW * 2] : 0.f;
-                float4 *d = reinterpret_cast<float4 *>(static_cast<float *>(out) + gofs);
-                d[0] = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                d[1] = make_float4(vv[4], vv[5], vv[6], vv[7]);
-            } else {
-                const __half *so = reinterpret_cast<const __half *>(sout + plane * G::SOUT) + st_soff[v];
-                __half vv[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) vv[k] = (m + k < T) ? so[k * G::OROW * 2] : __float2half(0.f);
-                __half *dst = static_cast<__half *>(plane ? out_lo : out);
-                *reinterpret_cast<uint4 *>(dst + gofs) = *reinterpret_cast<const uint4 *>(vv);
+            const int e = tid + v * NT;
+            const int plane = e / (G::NROW * G::PIECES);
+            const int e2 = e % (G::NROW * G::PIECES);
+            const int piece = (e2 >> 3) % G::PIECES;
+            const int row = (e2 & 7) + 8 * (e2 / (8 * G::PIECES));
+            const int li = row / (2 * C), c = (row >> 1) % C, comp = row & 1;
+            const int nn = n0 + li;
+            if (nn < N) {
+                const uint4 val = *reinterpret_cast<const uint4 *>(sout + plane * G::SOUT + (size_t)row * G::ORB + 16 * piece);
+                const long gofs = (((long)sb * C + c) * (2L * N) + 2L * nn + comp) * t_stride + m0 + piece * (16 / G::OE);
+                if (OUTK == OUT_F32) {
+                    *reinterpret_cast<uint4 *>(static_cast<float *>(out) + gofs) = val;
+                } else {
+                    __half *dst = static_cast<__half *>(plane ? out_lo : out);
+                    *reinterpret_cast<uint4 *>(dst + gofs) = val;
+                }
             }
         }
-        __syncthreads();
+        // no barrier here: the next writes to the staging buffer (pass 2) come
+        // after the next batch's deposit, FIR and pass-1 barriers
     }
 }
 
