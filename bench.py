@@ -195,6 +195,87 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
                 launches=launches, ops_per_step=ops / steps)
 
 
+def time_post(acf, torch, pk, N, n_sb, C, oracle_sample=True):
+    """The post-correlation kernels (delay compensation, channel integration by
+    4, two-stage sigma clip, lost-data weights for one second of 16-sample
+    packets, re-weighting) on a full A-12 visibility set [16][64][NB], each
+    timed with CUDA events through the C ABI (outputs preallocated), with the
+    numpy oracle timed on a bounded sample beside it."""
+    import ctypes
+    import numpy as np
+    from paper_1609_04205_b300 import _lib as A
+    L = A.lib()
+    NB = N * (N + 1) // 2
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(7)
+    V = torch.randn((n_sb, C, NB, 2), generator=g, device=dev)
+    Vout = torch.empty((n_sb, C // 4, NB, 2), device=dev)
+    flags = torch.empty((n_sb, C, NB), dtype=torch.uint8, device=dev)
+    nblk = 195313 // 16 + 1
+    mask = (torch.rand((nblk, N), generator=g, device=dev) < 0.97).to(torch.uint8)
+    W = torch.empty(NB, dtype=torch.int64, device=dev)
+    fs = 195312.5
+    d = np.ascontiguousarray(np.random.default_rng(3).uniform(-2e-6, 2e-6, N))
+    fc = np.ascontiguousarray((300 + np.arange(n_sb)) * fs)
+    vp = ctypes.c_void_p
+    hs = A.stream_handle(None)
+    vb = V.numel() * 4
+    ops = {
+        "delay_compensate": (lambda: L.acf_delay_compensate(A.ptr(V), n_sb, C, N, d.ctypes.data_as(vp),
+                                                             fc.ctypes.data_as(vp), fs, hs), 2 * vb, n_sb * C * NB),
+        "integrate_channels_by4": (lambda: L.acf_integrate_channels(A.ptr(V), A.ptr(Vout), n_sb, C, N, 4, 0, hs),
+                                   vb + vb // 4, n_sb * C * NB),
+        "sigma_clip": (lambda: L.acf_sigma_clip(A.ptr(V), A.ptr(flags), n_sb, C, N, 5.0, 3.0, hs),
+                       2 * vb + flags.numel(), n_sb * C * NB),
+        "lost_sample_weights": (lambda: L.acf_lost_sample_weights(A.ptr(mask), nblk, N, 16, A.ptr(W), hs),
+                                mask.numel() + W.numel() * 8, NB),
+        "reweight": (lambda: L.acf_reweight(A.ptr(V), A.ptr(W), 195313, n_sb * C, N, hs), 2 * vb + W.numel() * 8,
+                     n_sb * C * NB),
+    }
+    out = {}
+    for name, (fn, nbytes, elems) in ops.items():
+        for _ in range(2):
+            A.check(fn())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            A.check(fn())
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = dict(ms=ms, gbs=gbs, frac_hbm=gbs / pk["hbm"], bytes=nbytes, gpu_elems_per_s=elems / (ms * 1e-3))
+    out["workload"] = "A-12 visibilities: 16 subbands x 64 channels x 664128 baselines (5.44 GB cf32); " \
+                      "weights: 12208 blocks x 1152 inputs"
+    del V, Vout, flags, mask, W
+    torch.cuda.empty_cache()
+    if oracle_sample:
+        from oracle import post
+        rng = np.random.default_rng(5)
+        samples = {}
+        Vs = rng.normal(size=(1, 1, NB)) + 1j * rng.normal(size=(1, 1, NB))
+        t0 = time.perf_counter(); post.delay_compensate(Vs, d, fc[:1], fs); dt = time.perf_counter() - t0
+        samples["delay_compensate"] = (NB / dt, "1 channel of 1 subband, full triangle")
+        Vs = rng.normal(size=(1, C, 20000)) + 1j * rng.normal(size=(1, C, 20000))
+        t0 = time.perf_counter(); post.integrate_channels(Vs, 4); dt = time.perf_counter() - t0
+        samples["integrate_channels_by4"] = (C * 20000 / dt, "64 channels x 20000 baselines")
+        n2 = 128
+        Vs = rng.normal(size=(1, C, n2 * (n2 + 1) // 2)) + 1j * rng.normal(size=(1, C, n2 * (n2 + 1) // 2))
+        t0 = time.perf_counter(); post.sigma_clip(Vs, 5.0, 3.0); dt = time.perf_counter() - t0
+        samples["sigma_clip"] = (Vs.size / dt, "128 inputs x 64 channels")
+        m = (rng.uniform(size=(nblk, 64)) < 0.97)
+        t0 = time.perf_counter(); post.lost_sample_weights(m, 16); dt = time.perf_counter() - t0
+        samples["lost_sample_weights"] = (64 * 65 // 2 / dt, "64 inputs, 12208 blocks")
+        Vs = rng.normal(size=(1, 1, NB)) + 1j * rng.normal(size=(1, 1, NB))
+        Ws = rng.integers(1, 195313, NB)
+        t0 = time.perf_counter(); post.reweight(Vs, Ws, 195313); dt = time.perf_counter() - t0
+        samples["reweight"] = (NB / dt, "1 channel of 1 subband, full triangle")
+        for k, (v, what) in samples.items():
+            out[k]["cpu_baseline"] = dict(value=v, unit="elements/s", kind="oracle", cores=1, sample=what)
+    return out
+
+
 def aggregate(ms_local, ops_local, device="cpu"):
     """Whole-job figures across ranks: step time = max over ranks, value =
     the ops of all ranks over that time (weak scaling: each rank correlates
@@ -335,6 +416,10 @@ def main():
             e2e = dict(value=None, unit=UNIT, h2d_bytes_per_step=in_bytes, d2h_bytes_per_step=0,
                        note="e2e failed: %s" % ex)
 
+    post_r = None
+    if not args.quick:
+        post_r = time_post(acf, torch, pk, N, n_sb, w["n_channels"], oracle_sample=(rank == 0))
+
     cpu = None
     if rank == 0 and not args.quick:
         import oracle
@@ -361,7 +446,7 @@ def main():
                 roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
                 channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
                                  bytes=in_bytes + out_bytes),
-                e2e=e2e, cpu_baseline=cpu, modes=extra)
+                e2e=e2e, cpu_baseline=cpu, modes=extra, post=post_r)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

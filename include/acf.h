@@ -202,6 +202,82 @@ acf_status acf_xengine(acf_xmode mode, const void *x, const void *x_lo, int n_pr
                        int n_inputs, long n_time, long t_stride, float vscale, void *V,
                        acf_stream_t stream);
 
+/* ---- post-correlation steps on the visibilities ----------------------------
+ * V below is laid out as the correlator writes it: [n_subbands][n_channels][NB]
+ * with NB = n_inputs*(n_inputs+1)/2, complex float32 unless stated.  All are
+ * single passes over V (HBM-bound).  Scratch comes from the stream-ordered
+ * allocator (cudaMallocAsync on `stream`) and is released on the stream.
+ * Errors: EINVAL on the argument checks listed, ENOMEM when the scratch
+ * allocation fails, ECUDA when a launch fails; nothing is enqueued on EINVAL. */
+
+/* Delay compensation (Sec. 4.2.4: fixed cable delays applied as phase
+ * rotations of the visibilities).  With d_i the delay of input i relative to
+ * the reference (x_i(t) = r(t - d_i)):
+ *     V_ij <- V_ij * exp(+2 pi i f (d_i - d_j)),
+ * f = f_centre[s] + c' * sample_rate / n_channels, c' = c for 2c < n_channels
+ * and c - n_channels otherwise (the natural channel order of the filter bank;
+ * a raw subband, n_channels == 1, sits at f_centre).  Phases are reduced to
+ * turns in fp64 before the sine; the rotation is applied in fp32.
+ *   V        device, modified in place;
+ *   delays   host, n_inputs doubles (seconds), copied before return;
+ *   f_centre host, n_subbands doubles (Hz), copied before return.
+ * EINVAL: NULL pointer, a count < 1, n_subbands * n_channels > 65535,
+ * sample_rate not finite and > 0, a delay or frequency not finite. */
+acf_status acf_delay_compensate(void *V, int n_subbands, int n_channels, int n_inputs, const double *delays,
+                                const double *f_centre, double sample_rate, acf_stream_t stream);
+
+/* Apply the same delay compensation to every integration this context hands
+ * out through acf_get_visibilities (FP modes; the INT8 path keeps exact
+ * integers and gives EUNSUPPORTED).  The phase table is built on the device
+ * now (n_subbands * n_channels * n_inputs complex float32, owned by the
+ * context); delays == NULL switches compensation off again.  Only between
+ * integrations (ESTATE otherwise). */
+acf_status acf_set_delays(acf_ctx *ctx, const double *delays, const double *f_centre, double sample_rate);
+
+/* Channel integration to a coarser resolution (Sec. 4.2.4): output channel k
+ * of subband s is the sum of input channels k*group .. k*group + group - 1.
+ * `group` must divide n_channels and either equal it or divide n_channels/2,
+ * so that each group is contiguous in frequency in the natural channel
+ * order.  vis_int64 = 1 sums complex int64 visibilities (INT8 mode) exactly.
+ *   V_in   device [n_subbands][n_channels][NB];
+ *   V_out  device [n_subbands][n_channels/group][NB], written; must not
+ *          alias V_in.
+ * EINVAL: NULL or aliasing pointers, a count < 1, a group that breaks the
+ * rule above, grid limits (n_subbands or n_channels/group > 65535). */
+acf_status acf_integrate_channels(const void *V_in, void *V_out, int n_subbands, int n_channels, int n_inputs,
+                                  int group, int vis_int64, acf_stream_t stream);
+
+/* Two-stage sigma-clip flagging of visibility amplitudes (Sec. 4.3).
+ * Stage 1, per channel: flag cross-correlation V_ij when
+ *     |V_ij|^2 > k_chan^2 * mean over the channel's cross-correlations of |V|^2;
+ * stage 2, per baseline across the channels of its subband: flag channel c
+ * when |V_ij,c|^2 > k_vis^2 * mean of |V_ij|^2 over the channels stage 1
+ * kept.  Squares, sums and comparisons in fp64.  Autocorrelations are never
+ * used or flagged.
+ *   V      device, complex float32 (not modified);
+ *   flags  device uint8 [n_subbands][n_channels][NB], written (1 = flagged).
+ * EINVAL: NULL pointer, a count < 1, n_channels > 256, k not finite and > 0,
+ * more than 65535 subbands * channels. */
+acf_status acf_sigma_clip(const void *V, unsigned char *flags, int n_subbands, int n_channels, int n_inputs,
+                          double k_chan, double k_vis, acf_stream_t stream);
+
+/* Weighting matrix for lost data (Sec. 4.2.1: lost station packets; the
+ * weighting step of Sec. 4.3):  W_ij = samples_per_block * sum_b m_i[b] m_j[b]
+ * with m_i[b] = (mask[b][i] != 0), i.e. the number of samples both inputs
+ * delivered.  Computed as AND + popcount over bit-packed masks.
+ *   mask  device uint8 [n_blocks][n_inputs] (time-major like the samples);
+ *   W     device int64 [NB], written, packed like V.
+ * EINVAL: NULL pointer, a count < 1, n_blocks > 65535 * 32. */
+acf_status acf_lost_sample_weights(const unsigned char *mask, long n_blocks, int n_inputs, long samples_per_block,
+                                   long long *W, acf_stream_t stream);
+
+/* Re-weighting for lost data: V_ij <- V_ij * n_total / W_ij for every one of
+ * n_problems triangles (0 where W_ij == 0).  V device complex float32
+ * [n_problems][NB], in place; W device int64 [NB] as acf_lost_sample_weights
+ * writes it.  EINVAL: NULL pointer, n_total < 0, a count < 1, n_problems > 65535. */
+acf_status acf_reweight(void *V, const long long *W, long n_total, int n_problems, int n_inputs,
+                        acf_stream_t stream);
+
 /* ---- gain-corrupted correlation and its adjoint (calibration) ------------
  * Model M_c = G R_c G^H with G = diag(g); residual E_c = M_c - V_c;
  * loss L = sum_c ||E_c||_F^2 over the full Hermitian matrix;

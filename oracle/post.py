@@ -28,12 +28,12 @@ def channel_freqs(f_centre, sample_rate: float, n_channels: int) -> np.ndarray:
 
     The channeliser computes X_c = sum_n y[n] e^{-2 pi i c n / C} (natural
     order, no shift), so a baseband tone at +c fs / C lands in channel c:
-    channel c sits at f_centre + c' fs / C with c' = c for c < C/2 and
+    channel c sits at f_centre + c' fs / C with c' = c for 2c < C and
     c' = c - C otherwise (Sec. 4.2.3 filter bank; frequency order is a
-    documented reading)."""
+    documented reading).  A single channel (raw subband) sits at f_centre."""
     C = int(n_channels)
     c = np.arange(C)
-    off = np.where(c < C // 2, c, c - C) * (float(sample_rate) / C)
+    off = np.where(2 * c < C, c, c - C) * (float(sample_rate) / C)
     return np.asarray(f_centre, dtype=np.float64)[:, None] + off[None, :]
 
 

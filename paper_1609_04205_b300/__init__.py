@@ -9,3 +9,4 @@ from ._lib import AcfError, lib  # noqa: F401
 from .correlator import (Batch, Correlator, channelise, device_status, launch_count,  # noqa: F401
                          n_baselines, prototype, transpose_raw, xengine)
 from .gain import GainCorr, gain_grad, gain_loss_and_grad  # noqa: F401
+from . import postproc  # noqa: F401

@@ -28,6 +28,8 @@ EXPORTS = [
     "acf_gain_forward", "acf_gain_backward", "acf_batch_create", "acf_batch_run", "acf_batch_query",
     "acf_batch_destroy", "acf_batch_last_error", "acf_launch_count", "acf_device_status", "acf_version",
     "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc", "acf_set_xengine_variant",
+    "acf_delay_compensate", "acf_set_delays", "acf_integrate_channels", "acf_sigma_clip",
+    "acf_lost_sample_weights", "acf_reweight",
 ]
 
 
@@ -93,6 +95,12 @@ def lib():
         "acf_last_timing": ([P, ctypes.POINTER(F), ctypes.POINTER(F)], I),
         "acf_gain_forward_noalloc": ([P, P, P, I, I, P, P, P], I),
         "acf_set_xengine_variant": ([P, I], I),
+        "acf_delay_compensate": ([P, I, I, I, P, P, ctypes.c_double, P], I),
+        "acf_set_delays": ([P, P, P, ctypes.c_double], I),
+        "acf_integrate_channels": ([P, P, I, I, I, I, I, P], I),
+        "acf_sigma_clip": ([P, P, I, I, I, ctypes.c_double, ctypes.c_double, P], I),
+        "acf_lost_sample_weights": ([P, Lg, I, Lg, P, P], I),
+        "acf_reweight": ([P, P, Lg, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -66,6 +66,18 @@ class Correlator:
         """0: one SM per tile; 1: SM pairs sharing each 256x256 tile (cta_group::2)."""
         A.check(self._L.acf_set_xengine_variant(self._h, int(variant)), self._h)
 
+    def set_delays(self, delays, f_centre, sample_rate: float):
+        """Delay-compensate every integration handed out from now on (acf_set_delays);
+        delays=None switches it off."""
+        import numpy as np
+        if delays is None:
+            A.check(self._L.acf_set_delays(self._h, None, None, 0.0), self._h)
+            return
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.float64))
+        f = np.ascontiguousarray(np.asarray(f_centre, dtype=np.float64))
+        A.check(self._L.acf_set_delays(self._h, d.ctypes.data_as(ctypes.c_void_p), f.ctypes.data_as(ctypes.c_void_p),
+                                       float(sample_rate)), self._h)
+
     def set_input_scale(self, s: float):
         A.check(self._L.acf_set_input_scale(self._h, float(s)), self._h)
 

@@ -92,4 +92,15 @@ cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N
                         cudaStream_t s);
 int gain_partials_needed(int N, int C);
 
+// ---- post-correlation steps (post.cu) ------------------------------------------
+cudaError_t launch_delay_table(const double *d_delays, const double *d_fc, double fs, int n_sb, int C, int N,
+                               float2 *d_tab, cudaStream_t s);
+cudaError_t launch_delay_apply(float2 *V, const float2 *d_tab, long n_prob, int N, cudaStream_t s);
+cudaError_t launch_integrate(const void *in, void *out, int n_sb, int C, int N, int G, int int64, cudaStream_t s);
+cudaError_t launch_sigma_clip(const float2 *V, int n_sb, int C, int N, double k1, double k2, double *d_sums,
+                              unsigned char *flags, cudaStream_t s);
+cudaError_t launch_weights(const unsigned char *mask, long n_blocks, int N, long spb, uint32_t *d_bits, long long *W,
+                           cudaStream_t s);
+cudaError_t launch_reweight(float2 *V, const long long *W, long n_total, int n_prob, int N, cudaStream_t s);
+
 }  // namespace acf

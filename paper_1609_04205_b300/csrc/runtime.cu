@@ -74,6 +74,7 @@ struct acf_ctx {
     long last_T = 0;
     bool timing = false, timed = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    float2 *d_delay_tab = nullptr;  // delay-compensation phases [n_sb * C][N], or NULL (off)
     std::string err;
 };
 
@@ -487,12 +488,57 @@ acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_
     if (!out || !n_ready) return fail(c, ACF_EINVAL, "out / n_ready is NULL");
     *n_ready = 0;
     if (!c->ready) return ACF_OK;
-    cudaError_t e = cudaMemcpyAsync(out, c->d_V, c->v_bytes, cudaMemcpyDefault, (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    if (c->d_delay_tab) {
+        // the accumulator is reset when the next integration starts, so rotate it in place
+        e = launch_delay_apply(static_cast<float2 *>(c->d_V), c->d_delay_tab, (long)c->n_sb * c->C, c->N,
+                               (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "delay compensation");
+    }
+    e = cudaMemcpyAsync(out, c->d_V, c->v_bytes, cudaMemcpyDefault, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "copy visibilities");
     *n_ready = 1;
     c->ready = false;
     c->v_valid = false;
     return ACF_OK;
+}
+
+acf_status acf_set_delays(acf_ctx *c, const double *delays, const double *f_centre, double sample_rate)
+{
+    if (!c) return ACF_EINVAL;
+    if (c->pushes != 0) return fail(c, ACF_ESTATE, "delays can only change between integrations");
+    if (!delays) {
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(c->d_delay_tab);
+        c->d_delay_tab = nullptr;
+        return e == cudaSuccess ? ACF_OK : cuda_fail(c, e, "sync");
+    }
+    if (c->mode == ACF_X_INT8) return fail(c, ACF_EUNSUPPORTED, "INT8 visibilities stay exact integers");
+    if (!f_centre || !(sample_rate > 0.0) || !std::isfinite(sample_rate))
+        return fail(c, ACF_EINVAL, "f_centre is NULL or sample_rate is not finite and positive");
+    for (int i = 0; i < c->N; ++i)
+        if (!std::isfinite(delays[i])) return fail(c, ACF_EINVAL, "non-finite delay");
+    for (int k = 0; k < c->n_sb; ++k)
+        if (!std::isfinite(f_centre[k])) return fail(c, ACF_EINVAL, "non-finite centre frequency");
+    const long n_prob = (long)c->n_sb * c->C;
+    if (n_prob > 65535) return fail(c, ACF_EINVAL, "more than 65535 subbands x channels");
+    double *tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, sizeof(double) * ((size_t)c->N + c->n_sb));
+    if (e != cudaSuccess) return fail(c, ACF_ENOMEM, "delay staging");
+    if (!c->d_delay_tab) {
+        e = cudaMalloc(&c->d_delay_tab, sizeof(float2) * (size_t)n_prob * c->N);
+        if (e != cudaSuccess) {
+            c->d_delay_tab = nullptr;
+            cudaFree(tmp);
+            return fail(c, ACF_ENOMEM, "delay table");
+        }
+    }
+    e = cudaMemcpy(tmp, delays, sizeof(double) * c->N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tmp + c->N, f_centre, sizeof(double) * c->n_sb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_delay_table(tmp, tmp + c->N, sample_rate, c->n_sb, c->C, c->N, c->d_delay_tab, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    return e == cudaSuccess ? ACF_OK : cuda_fail(c, e, "delay table");
 }
 
 acf_status acf_visibilities_device(acf_ctx *c, const void **p)
@@ -552,6 +598,7 @@ acf_status acf_destroy(acf_ctx *c)
     cudaFree(c->d_Xlo);
     cudaFree(c->d_V);
     cudaFree(c->d_stage);
+    cudaFree(c->d_delay_tab);
     for (auto ev : c->ev_copied) cudaEventDestroy(ev);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->plan) tc_plan_destroy(c->plan);
