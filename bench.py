@@ -276,6 +276,72 @@ def time_post(acf, torch, pk, N, n_sb, C, oracle_sample=True):
     return out
 
 
+def time_batch(acf, torch, synth, pk, steps=10):
+    """Ragged batch: 32 independent arrays (48-576 antennas, 16/64/256 channels
+    or raw, 0.25 s each; half raw INT8-exact, half channelised split FP16) run
+    as one persistent work list in one CUDA graph, autotuned.  Useful X-engine
+    ops over the CUDA-event time of whole batch runs (channelisers included)."""
+    jobs = synth.ragged_jobs()
+    b = acf.Batch(jobs, autotune=True)
+    ins = [synth.voltages(j["n_inputs"], j["n_samples"], 1, "ci8", 16.0, None, j["seed"], device="cuda")[0]
+           for j in jobs]
+    outs = b.outputs()
+    for _ in range(3):                      # autotune, graph capture, warm replay
+        b.run(ins, outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.run(ins, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    useful = issued = 0.0
+    for j in jobs:
+        C, P, S, N = j["n_channels"], j["n_taps"], j["n_samples"], j["n_inputs"]
+        T = S if C == 1 else (S - (P - 1) * C) // C
+        ops = xops(N, T, C, 1)
+        useful += ops
+        issued += ops if C == 1 else 3 * ops
+    q = b.query()
+    b.close()
+    tops = useful / (ms * 1e-3) / 1e12
+    return dict(ms=ms, useful_tops=tops, issued_tensor_tops=issued / (ms * 1e-3) / 1e12,
+                frac_of_sustained_issued=issued / (ms * 1e-3) / 1e12 / pk["bf16_sus"], tuning=q,
+                workload="32 arrays: 96-1152 inputs, 16/64/256 channels or raw, 48828 ci8 samples each; "
+                         "raw jobs INT8 exact, channelised jobs split FP16; one CUDA-graph replay per run")
+
+
+def time_gain(acf, torch, pk, N=576, C=64, steps=20):
+    """Gain forward (loss) + adjoint (gradient) in one pass over packed R and V:
+    576 inputs, 64 channels, complex float32."""
+    from paper_1609_04205_b300 import _lib as A
+    L = A.lib()
+    NB = N * (N + 1) // 2
+    g0 = torch.Generator(device="cuda").manual_seed(11)
+    R = torch.randn((C, NB, 2), generator=g0, device="cuda")
+    V = torch.randn((C, NB, 2), generator=g0, device="cuda")
+    g = torch.randn((N, 2), generator=g0, device="cuda")
+    loss = torch.empty((), device="cuda")
+    grad = torch.empty((N, 2), device="cuda")
+    hs = A.stream_handle(None)
+    run = lambda: A.check(L.acf_gain_forward(A.ptr(R), A.ptr(V), A.ptr(g), N, C, A.ptr(loss), A.ptr(grad), hs))
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nbytes = 2 * C * NB * 8
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return dict(ms=ms, gbs=gbs, frac_hbm=gbs / pk["hbm"], bytes=nbytes,
+                workload="576 inputs x 64 channels, packed R and V complex float32 (loss + gradient)")
+
+
 def aggregate(ms_local, ops_local, device="cpu"):
     """Whole-job figures across ranks: step time = max over ranks, value =
     the ops of all ranks over that time (weak scaling: each rank correlates
@@ -416,9 +482,11 @@ def main():
             e2e = dict(value=None, unit=UNIT, h2d_bytes_per_step=in_bytes, d2h_bytes_per_step=0,
                        note="e2e failed: %s" % ex)
 
-    post_r = None
+    post_r = batch_r = gain_r = None
     if not args.quick:
         post_r = time_post(acf, torch, pk, N, n_sb, w["n_channels"], oracle_sample=(rank == 0))
+        batch_r = time_batch(acf, torch, synth, pk)
+        gain_r = time_gain(acf, torch, pk)
 
     cpu = None
     if rank == 0 and not args.quick:
@@ -446,7 +514,7 @@ def main():
                 roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
                 channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
                                  bytes=in_bytes + out_bytes),
-                e2e=e2e, cpu_baseline=cpu, modes=extra, post=post_r)
+                e2e=e2e, cpu_baseline=cpu, modes=extra, post=post_r, ragged_batch=batch_r, gain=gain_r)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -70,6 +70,13 @@ struct acf_batch {
     TcPlan *plan = nullptr;
     cudaStream_t s_int = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // per-job preparation (channeliser or raw transpose) forks onto these
+    // streams so that small jobs run side by side; the X-engine joins them
+    static constexpr int kAux = 4;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t aux_done[kAux] = {};
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<int> aux_of;           // job -> aux stream (longest work first, least loaded)
     cudaGraphExec_t gexec = nullptr;
     std::vector<const void *> g_in;
     std::vector<void *> g_out;
@@ -104,27 +111,59 @@ static std::vector<TcJob> tc_jobs(const acf_batch *b, void *const *outputs)
     return v;
 }
 
-// Enqueue the whole batch (no graph) on stream s.
+// Enqueue the whole batch on stream s: the jobs' preparation forks across the
+// auxiliary streams (graph branches when captured), then one X-engine launch.
 static cudaError_t enqueue_all(acf_batch *b, const void *const *inputs, void *const *outputs, cudaStream_t s)
 {
     cudaError_t e;
+    if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return e;
+    for (int a = 0; a < acf_batch::kAux; ++a)
+        if ((e = cudaStreamWaitEvent(b->aux[a], b->ev_fork, 0)) != cudaSuccess) return e;
     for (size_t k = 0; k < b->jobs.size(); ++k) {
         const acf_job &J = b->jobs[k];
+        cudaStream_t sk = b->aux[b->aux_of[k]];
         if (b->T[k] == 0 || !tc_plan_job_stores(b->plan, (int)k))
-            if ((e = cudaMemsetAsync(outputs[k], 0, b->v_bytes[k], s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(outputs[k], 0, b->v_bytes[k], sk)) != cudaSuccess) return e;
         if (b->T[k] == 0) continue;
         if (J.n_channels == 1) {
             e = launch_transpose_raw(inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, OUT_F16, b->X[k], nullptr,
-                                     b->t_stride[k], 1.f, s);
+                                     b->t_stride[k], 1.f, sk);
         } else {
             e = launch_channelise(nullptr, 0, inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, J.n_channels, J.n_taps,
                                   b->d_h[(long)J.n_taps * 1024 + J.n_channels], b->d_bp[J.n_channels],
                                   b->d_tw[J.n_channels], OUT_F16X3, b->X[k], b->Xlo[k], b->t_stride[k], b->scale[k],
-                                  b->T[k], s);
+                                  b->T[k], sk);
         }
         if (e != cudaSuccess) return e;
     }
+    for (int a = 0; a < acf_batch::kAux; ++a) {
+        if ((e = cudaEventRecord(b->aux_done[a], b->aux[a])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, b->aux_done[a], 0)) != cudaSuccess) return e;
+    }
     return tc_plan_launch(b->plan, s);
+}
+
+// Jobs to auxiliary streams: longest preparation first onto the least-loaded
+// stream (cost ~ samples x inputs, x4 for a filter bank).
+static void assign_aux(acf_batch *b)
+{
+    const size_t n = b->jobs.size();
+    std::vector<int> order(n);
+    std::vector<double> cost(n);
+    for (size_t k = 0; k < n; ++k) {
+        order[k] = (int)k;
+        cost[k] = (double)b->jobs[k].n_samples * b->jobs[k].n_inputs * (b->jobs[k].n_channels > 1 ? 4.0 : 1.0);
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    double load[acf_batch::kAux] = {};
+    b->aux_of.assign(n, 0);
+    for (int k : order) {
+        int best = 0;
+        for (int a = 1; a < acf_batch::kAux; ++a)
+            if (load[a] < load[best]) best = a;
+        b->aux_of[k] = best;
+        load[best] += cost[k];
+    }
 }
 
 static cudaError_t rebuild_plan(acf_batch *b, void *const *outputs, const TcTuning &tun)
@@ -264,6 +303,13 @@ acf_status acf_batch_create(acf_batch **out, const acf_job *jobs, int n_jobs, in
     if ((e = cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking)) != cudaSuccess) return cleanup(ACF_ECUDA, "stream");
     cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (int a = 0; a < acf_batch::kAux; ++a) {
+        if ((e = cudaStreamCreateWithFlags(&b->aux[a], cudaStreamNonBlocking)) != cudaSuccess)
+            return cleanup(ACF_ECUDA, "aux stream");
+        cudaEventCreateWithFlags(&b->aux_done[a], cudaEventDisableTiming);
+    }
+    assign_aux(b);
     if (tune) autotune(b);
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(ACF_ECUDA, "device error during planning");
     *out = b;
@@ -338,6 +384,11 @@ acf_status acf_batch_destroy(acf_batch *b)
     for (auto &kv : b->d_bp) cudaFree(kv.second);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    for (int a = 0; a < acf_batch::kAux; ++a) {
+        if (b->aux_done[a]) cudaEventDestroy(b->aux_done[a]);
+        if (b->aux[a]) cudaStreamDestroy(b->aux[a]);
+    }
     if (b->s_int) cudaStreamDestroy(b->s_int);
     delete b;
     cudaGetLastError();

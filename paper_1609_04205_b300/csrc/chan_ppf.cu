@@ -98,6 +98,31 @@ k_channelise(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in
         __syncthreads();
         // 2. FIR: y_m[c] = sum_k h[kC + c] u[(m + k) C + c]
         constexpr int PAIRS = NI * C;
+        if (P == 16) {
+            // 16 taps: per (input, phase) the taps sit in registers and the
+            // batch's MS + 15 samples slide through a register window, so a
+            // sample is read from shared memory once per batch, not per tap
+            for (int w = tid; w < PAIRS; w += kThreads) {
+                const int c = w % C, ni = w / C;
+                float hk[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) hk[k] = __ldg(h + k * C + c);
+                float2 u[MS + 15];
+#pragma unroll
+                for (int r = 0; r < MS + 15; ++r) u[r] = InT<IN>::f(win[(r * C + c) * NI + ni]);
+#pragma unroll
+                for (int mm = 0; mm < MS; ++mm) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        acc.x = fmaf(hk[k], u[mm + k].x, acc.x);
+                        acc.y = fmaf(hk[k], u[mm + k].y, acc.y);
+                    }
+                    ybuf[(ni * MS + mm) * C + c] = acc;
+                }
+            }
+        } else
+        {
         constexpr int G = PAIRS >= kThreads ? 1 : kThreads / PAIRS;
         constexpr int MSG = MS / G > 0 ? MS / G : 1;
         for (int w = tid; w < PAIRS * G; w += kThreads) {
@@ -114,6 +139,7 @@ k_channelise(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in
                 }
                 ybuf[(ni * MS + mm) * C + c] = acc;
             }
+        }
         }
         __syncthreads();
         // 3. FFT per (input, spectrum)
