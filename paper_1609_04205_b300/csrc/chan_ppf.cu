@@ -318,7 +318,14 @@ cudaError_t launch_t(const void *hist, long n_hist, const void *samples, long n_
 {
     const long T64 = round_up(T, 64);
     if (T64 == 0) return cudaSuccess;
-    const long m_per_block = 256;
+    // Every batch re-stages its own FIR windows, so a shorter time segment per
+    // block costs nothing extra: halve it until the grid fills the GPU.
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long groups = (N + NI - 1) / NI;
+    long m_per_block = 256;
+    while (m_per_block > MS && groups * n_sb * ((T64 + m_per_block - 1) / m_per_block) < 4L * sms) m_per_block /= 2;
     const size_t smem = C * sizeof(float2) + (size_t)NI * MS * C * sizeof(float2) +
                         (size_t)(MS + P - 1) * C * NI * sizeof(IN);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
