@@ -380,6 +380,19 @@ def profile_case(mode):
     return 0
 
 
+def post_case():
+    """The post-correlation kernels alone on the A-12 visibility set (the same
+    calls as the bench line's `post` object, without the oracle), for profiling."""
+    import torch
+
+    import paper_1609_04205_b300 as acf
+    r = time_post(acf, torch, peaks(), 1152, 16, 64, oracle_sample=False)
+    for k, v in r.items():
+        if isinstance(v, dict):
+            print("%-26s %8.3f ms %8.1f GB/s  frac %.3f" % (k, v["ms"], v["gbs"], v["frac_hbm"]))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,6 +400,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="acf", choices=["acf", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the comparison modes and the e2e pass")
+    ap.add_argument("--post-case", action="store_true",
+                    help="run only the post-correlation kernels on the A-12 visibility set (profiling)")
     ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8"], default=None,
                     help="small case for ncu captures: one subband of the default workload (one raw "
                          "A-6 subband for int8), warm-up plus three pushes, no JSON line")
@@ -395,6 +410,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return profile_case(args.profile_case)
+    if args.post_case:
+        return post_case()
 
     import torch
 
