@@ -38,8 +38,15 @@ def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"], src="measured")
-    return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"], src="measured",
+                    sm_max_mhz=d.get("sm_max_mhz", 2032.0))
+    return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback", sm_max_mhz=2032.0)
+
+
+def fp32_fma_peak_tflops(torch, sm_max_mhz):
+    """FP32 FMA peak of the device: SMs x 128 lanes x 2 flops x max SM clock."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 def xeng_traffic_per_subband():
@@ -449,7 +456,9 @@ def main():
         extra["fp16x3"] = dict(tops=r3["tops"], xeng_tops=r3["xeng_tops"], ms_per_step=r3["ms_per_step"],
                                issued_tensor_tops=3 * r3["xeng_tops"])
         r32 = time_mode(acf, torch, x, w, "fp32", 2, 1, stream)
-        extra["fp32_cuda_core"] = dict(tops=r32["tops"], xeng_tops=r32["xeng_tops"], ms_per_step=r32["ms_per_step"])
+        fp32_peak = fp32_fma_peak_tflops(torch, pk["sm_max_mhz"])
+        extra["fp32_cuda_core"] = dict(tops=r32["tops"], xeng_tops=r32["xeng_tops"], ms_per_step=r32["ms_per_step"],
+                                       fp32_fma_peak_tflops=fp32_peak, frac_of_fp32_peak=r32["xeng_tops"] / fp32_peak)
         extra["fp16_speedup_vs_fp32_path"] = main_r["tops"] / r32["tops"]
         extra["fp16x3_speedup_vs_fp32_path"] = r3["tops"] / r32["tops"]
         # INT8-exact raw subbands, AARTFAAC-6 shape
@@ -461,6 +470,9 @@ def main():
                             device=dev)
         r8 = time_mode(acf, torch, x6, w6, "int8", max(2, args.steps // 2), 2, stream)
         extra["int8_raw_a6"] = dict(tops=r8["tops"], xeng_tops=r8["xeng_tops"], ms_per_step=r8["ms_per_step"],
+                                    frac_of_fp16_sustained=r8["xeng_tops"] / pk["bf16_sus"],
+                                    note="exact INT8 runs on the fp16 tensor path (kind::i8 does not assemble "
+                                         "for sm_103a), so its peak is the fp16 one",
                                     workload="576 inputs x 8 subbands x 195313 ci8 samples, raw subband, exact")
         del x6
         torch.cuda.empty_cache()
