@@ -100,7 +100,10 @@ acf_status acf_set_input_scale(acf_ctx *ctx, float s);
 /* Push n_samples new samples per subband: `samples` device,
  * [n_subbands][n_samples][n_inputs] complex of the context's dtype.  The
  * samples are consumed in stream order on `stream`; the buffer may be reused
- * once that work completes.  1 <= n_samples <= max_samples.
+ * once that work completes.  1 <= n_samples <= max_samples; n_samples need
+ * not be a multiple of n_channels (a one-second subband block holds 195,313
+ * samples): samples past the last complete spectrum stay in the filter
+ * history and open the next push's first spectrum.
  * Errors: EINVAL (NULL, size), ESTATE when the previous integration is
  * complete and has not been read, ETIMEOUT / ECUDA from the device. */
 acf_status acf_push_block(acf_ctx *ctx, const void *samples, long n_samples,
