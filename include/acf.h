@@ -300,21 +300,26 @@ acf_status acf_gain_backward(const void *R, const void *V, const void *g, int n_
                              int n_channels, void *grad, acf_stream_t stream);
 
 /* Same as acf_gain_forward, but allocates nothing: for callers that cannot
- * call cudaMalloc (work recorded inside a CUDA-graph capture, processes whose
- * device memory is reserved up front, plug-ins that must not touch the
- * allocator).  This entry point has no counterpart in the paper; it is a
- * deployment convenience.
+ * call cudaMalloc while they run (processes whose device memory is reserved
+ * up front, real-time loops that must not block in the allocator, plug-ins of
+ * a framework that owns every allocation).  This entry point has no
+ * counterpart in the paper; it is a deployment convenience.
  *   - The per-block loss partials live in a fixed device array inside the
  *     library of 65,536 floats (256 KiB), held by every GPU that loads the
  *     library until the process exits.  Problems needing more partials than
  *     that -- ceil(n_inputs/64) * (ceil(n_inputs/64) + 1) / 2 * n_channels
- *     > 65,536 -- are rejected with ACF_EINVAL; acf_gain_forward handles them.
+ *     > 65,536, counted in 64 bits -- are rejected with ACF_EINVAL before
+ *     anything is enqueued; acf_gain_forward handles them.
  *   - The first call on a device looks up the array's device address (no
- *     allocation); make that first call before any stream capture.
+ *     allocation) and keeps it; make that first call before any stream
+ *     capture.  cudaDeviceReset unloads the library's device image and would
+ *     leave the kept address stale: do not reset the device between calls.
  *   - All calls share the array, so calls that may overlap on the GPU (on
  *     different streams without ordering) race; serialise them.
- *   - The array is fully rewritten by each call; `grad` is zeroed on `stream`
- *     before it is accumulated.  Arguments and results as acf_gain_forward. */
+ *   - Each call rewrites the partials it reads (the array keeps the last
+ *     call's contents, none of which a later call depends on); `grad` is
+ *     zeroed on `stream` before it is accumulated.  Arguments and results as
+ *     acf_gain_forward; n_channels <= 65535. */
 acf_status acf_gain_forward_noalloc(const void *R, const void *V, const void *g, int n_inputs,
                                     int n_channels, float *loss, void *grad, acf_stream_t stream);
 

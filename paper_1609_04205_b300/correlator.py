@@ -212,15 +212,6 @@ class Batch:
         outs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outputs])
         A.check(self._L.acf_batch_run(self._h, ins, outs, A.stream_handle(stream)), batch=self._h)
 
-    def enable_timing(self, on=True):
-        A.check(self._L.acf_enable_timing(self._h, 1 if on else 0), self._h)
-
-    def last_timing(self):
-        """(channeliser ms, X-engine ms) of the last push (CUDA events)."""
-        a, b = ctypes.c_float(), ctypes.c_float()
-        A.check(self._L.acf_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
-        return a.value, b.value
-
     def query(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         A.check(self._L.acf_batch_query(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), batch=self._h)

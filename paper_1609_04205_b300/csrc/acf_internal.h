@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "acf.h"
 
@@ -22,6 +23,10 @@ enum OutKind { OUT_F32 = 0, OUT_F16 = 1, OUT_F16X3 = 2 };
 inline int in_elem_bytes(acf_in_dtype d) { return d == ACF_IN_CI8 ? 2 : d == ACF_IN_CI16 ? 4 : 8; }
 inline long round_up(long a, long b) { return (a + b - 1) / b * b; }
 inline long n_baselines(long n) { return n * (n + 1) / 2; }
+
+// Filter-bank prototype (Sec. 4.2.3): Hann-windowed sinc of length P*C, unit
+// sum, evaluated in double and rounded to float (runtime.cu).
+void prototype_host(int P, int C, std::vector<float> &h);
 
 // ---- channeliser (chan_ppf.cu) -------------------------------------------
 // Twiddle table exp(-2 pi i k / C), k < C, float2, device.
@@ -88,9 +93,10 @@ bool tc_supported(int device);
 
 // ---- gain (gain.cu) ---------------------------------------------------------
 cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N, int C,
-                        float *loss, float2 *grad, float *partials, int n_partials_cap,
+                        float *loss, float2 *grad, float *partials, long long n_partials_cap,
                         cudaStream_t s);
-int gain_partials_needed(int N, int C);
+// Loss partials a gain launch needs (64-bit: ceil(N/64)(ceil(N/64)+1)/2 * C).
+long long gain_partials_needed(int N, int C);
 
 // ---- post-correlation steps (post.cu) ------------------------------------------
 cudaError_t launch_delay_table(const double *d_delays, const double *d_fc, double fs, int n_sb, int C, int N,

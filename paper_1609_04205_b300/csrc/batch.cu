@@ -26,25 +26,6 @@ long spectra_of(long len, int P, int C)
     return len < L ? 0 : (len - L) / C + 1;
 }
 
-void proto(int P, int C, std::vector<float> &h)
-{
-    const long L = (long)P * C;
-    h.assign(L, 0.f);
-    if (L == 1) {
-        h[0] = 1.f;
-        return;
-    }
-    std::vector<double> d(L);
-    double sum = 0;
-    for (long n = 0; n < L; ++n) {
-        const double w = 0.5 - 0.5 * std::cos(2.0 * M_PI * (double)n / (double)(L - 1));
-        const double u = ((double)n - 0.5 * (double)(L - 1)) / (double)C;
-        const double s = (u == 0.0) ? 1.0 : std::sin(M_PI * u) / (M_PI * u);
-        d[n] = w * s;
-        sum += d[n];
-    }
-    for (long n = 0; n < L; ++n) h[n] = (float)(d[n] / sum);
-}
 }  // namespace
 }  // namespace acf
 
@@ -276,7 +257,7 @@ acf_status acf_batch_create(acf_batch **out, const acf_job *jobs, int n_jobs, in
         if (!raw) {
             const long key = (long)J.n_taps * 1024 + J.n_channels;
             std::vector<float> h;
-            proto(J.n_taps, J.n_channels, h);
+            prototype_host(J.n_taps, J.n_channels, h);
             if (!b->d_h.count(key)) {
                 float *d = nullptr;
                 if ((e = cudaMalloc(&d, sizeof(float) * h.size())) != cudaSuccess) return cleanup(ACF_ENOMEM, "alloc");

@@ -112,11 +112,11 @@ k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 
 }
 
 // Fixed-order pairwise reduction of the partials into *loss.
-__global__ void __launch_bounds__(1024) k_reduce(const float *__restrict__ part, int n, float *loss)
+__global__ void __launch_bounds__(1024) k_reduce(const float *__restrict__ part, long long n, float *loss)
 {
     __shared__ float s[1024];
     float acc = 0.f;
-    for (int k = threadIdx.x; k < n; k += 1024) acc += part[k];
+    for (long long k = threadIdx.x; k < n; k += 1024) acc += part[k];
     s[threadIdx.x] = acc;
     __syncthreads();
     for (int w = 512; w >= 1; w >>= 1) {
@@ -128,25 +128,28 @@ __global__ void __launch_bounds__(1024) k_reduce(const float *__restrict__ part,
 
 }  // namespace
 
-int gain_partials_needed(int N, int C)
+long long gain_partials_needed(int N, int C)
 {
-    const int nt = (N + GT - 1) / GT;
-    return nt * (nt + 1) / 2 * C;
+    // 64-bit throughout: for millions of inputs the tile count alone passes 2^31
+    const long long nt = ((long long)N + GT - 1) / GT;
+    return nt * (nt + 1) / 2 * (long long)C;
 }
 
 cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N, int C,
-                        float *loss, float2 *grad, float *partials, int n_partials_cap,
+                        float *loss, float2 *grad, float *partials, long long n_partials_cap,
                         cudaStream_t s)
 {
-    const int nt = (N + GT - 1) / GT;
-    const int tiles = nt * (nt + 1) / 2;
+    const long long nt = ((long long)N + GT - 1) / GT;
+    const long long tiles = nt * (nt + 1) / 2;
+    // grid x holds the tiles of one channel, grid y the channels
+    if (N < 1 || C < 1 || C > 65535 || tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (tiles * C > n_partials_cap) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     if (grad) {
         e = cudaMemsetAsync(grad, 0, sizeof(float2) * N, s);
         if (e != cudaSuccess) return e;
     }
-    k_gain<<<dim3(tiles, C), 256, 0, s>>>(R, V, g, N, partials, grad);
+    k_gain<<<dim3((unsigned)tiles, (unsigned)C), 256, 0, s>>>(R, V, g, N, partials, grad);
     g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (loss) {
@@ -161,11 +164,11 @@ cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of acf_gain_forward for callers that cannot call
-// cudaMalloc: code running inside a CUDA-graph capture or under a strict
-// memory budget, embedded hosts whose device memory is carved up in advance,
-// or plug-ins of a framework that owns all allocations.  The loss partials
-// live in a fixed array in this library's device image instead of a buffer
-// the library allocates.  Every GPU that loads the library holds the array
+// cudaMalloc while they run: processes whose device memory is reserved up
+// front, real-time loops that must not block in the allocator, and plug-ins of
+// a framework that owns every allocation.  The loss partials live in a fixed
+// array in this library's device image instead of a buffer the library
+// allocates.  Every GPU that loads the library holds the array
 // (kGainStaticPartials floats) until the process exits.
 // ---------------------------------------------------------------------------
 namespace acf {
@@ -177,8 +180,11 @@ std::mutex g_static_mu;
 constexpr int kMaxDevices = 64;
 float *g_static_ptr[kMaxDevices] = {nullptr};        // device address per device, set once
 
-// Device address of the static array for the current device.  Host code may not
-// use the symbol itself (it is a host-side stand-in, not a device pointer).
+// Device address of the static array for the current device, looked up on the
+// first call on that device and kept.  Host code may not use the symbol itself
+// (it is a host-side stand-in, not a device pointer).  cudaDeviceReset unloads
+// the module, so an address kept from before a reset would be stale: the
+// entry point's contract forbids resetting the device between calls.
 cudaError_t static_partials(float **out)
 {
     int dev = 0;
@@ -202,9 +208,11 @@ extern "C" acf_status acf_gain_forward_noalloc(const void *R, const void *V, con
                                                int n_channels, float *loss, void *grad, acf_stream_t stream)
 {
     using namespace acf;
-    if (!R || !V || !g || n_inputs < 1 || n_channels < 1 || (!loss && !grad)) return ACF_EINVAL;
-    const long need = (long)gain_partials_needed(n_inputs, n_channels);
-    if (need > kGainStaticPartials) return ACF_EINVAL;       // beyond the fixed scratch
+    if (!R || !V || !g || n_inputs < 1 || n_channels < 1 || n_channels > 65535 || (!loss && !grad))
+        return ACF_EINVAL;
+    // checked before any CUDA call: a size beyond the fixed scratch never launches
+    const long long need = gain_partials_needed(n_inputs, n_channels);
+    if (need > kGainStaticPartials) return ACF_EINVAL;
     float *part = nullptr;
     if (static_partials(&part) != cudaSuccess) return ACF_ECUDA;
     cudaError_t e = launch_gain(static_cast<const float2 *>(R), static_cast<const float2 *>(V),

@@ -23,7 +23,7 @@ std::atomic<long long> g_launches{0};
 namespace {
 std::mutex g_mu;
 std::map<int, int *> g_err_words;          // device -> error word
-std::map<int, std::pair<float *, int>> g_gain_scratch;   // device -> (partials, capacity)
+std::map<int, std::pair<float *, long long>> g_gain_scratch;   // device -> (partials, capacity)
 thread_local std::string g_create_err;
 }  // namespace
 
@@ -92,7 +92,7 @@ static acf_status cuda_fail(acf_ctx *c, cudaError_t e, const char *where)
 static bool valid_channels(int c) { return c == 1 || c == 16 || c == 64 || c == 256; }
 
 // Sec. 4.2.3 prototype in double, rounded to float (same reading as the oracle).
-static void prototype_host(int P, int C, std::vector<float> &h)
+void acf::prototype_host(int P, int C, std::vector<float> &h)
 {
     const long L = (long)P * C;
     h.assign(L, 0.f);
@@ -700,8 +700,9 @@ acf_status acf_xengine(acf_xmode mode, const void *x, const void *x_lo, int n_pr
 static acf_status gain_common(const void *R, const void *V, const void *g, int N, int C, float *loss, void *grad,
                               cudaStream_t s)
 {
-    if (!R || !V || !g || N < 1 || C < 1) return ACF_EINVAL;
-    const int need = gain_partials_needed(N, C);
+    if (!R || !V || !g || N < 1 || C < 1 || C > 65535) return ACF_EINVAL;
+    const long long need = gain_partials_needed(N, C);
+    if ((need / C) > 0x7fffffffLL) return ACF_EINVAL;       // tiles of one channel fill grid x
     float *part = nullptr;
     {
         int dev = 0;

@@ -943,10 +943,8 @@ cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale, int s
     if (job < 0 || job >= p->params.n_jobs) return cudaErrorInvalidValue;
     JobDev &D = p->params.jobs[p->slot_of[job]];
     const long K64 = round_up(n_time, 64);
-    const long old64 = round_up(D.n_time, 64);
     // the time split was sized for the planned length; refuse a longer one
     if (D.mode == ACF_X_INT8 && (K64 + D.k_split - 1) / D.k_split > kInt8ItemMax) return cudaErrorInvalidValue;
-    (void)old64;
     D.n_time = n_time;
     D.vscale = vscale;
     D.store = (store && D.k_split == 1) ? 1 : 0;

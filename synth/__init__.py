@@ -128,7 +128,7 @@ def bandpass_ripple(n_channels: int, seed: int) -> np.ndarray:
     return (1.0 + 0.1 * np.cos(2 * np.pi * c / max(n_channels, 1)) + 0.02 * rng.standard_normal(n_channels)).astype(np.float32)
 
 
-# Workloads shaped like the paper's arrays (Sec. 2.1, 4, Table 1); see the design doc.
+# Workloads shaped like the paper's arrays (Sec. 2.1, 4, Table 1).
 WORKLOADS = {
     "tiny": dict(n_inputs=96, n_subbands=1, n_samples=19532, dtype="ci8", sigma=16.0,
                  n_channels=64, n_taps=16, n_sources=1, flux=0.2, seed=1001),

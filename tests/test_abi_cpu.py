@@ -87,3 +87,21 @@ def test_library_prototype_matches_oracle(P, C):
     ref = oracle.prototype(P, C)
     assert np.max(np.abs(h - ref)) <= 1e-7 * np.max(np.abs(ref)) + 1e-12
     assert L.acf_prototype(0, C, h.ctypes.data_as(ctypes.c_void_p)) == A.EINVAL
+
+
+@pytest.mark.parametrize("entry", ["acf_gain_forward_noalloc", "acf_gain_forward"])
+def test_gain_rejects_sizes_whose_partial_count_overflows_32_bits(entry):
+    """2,900,000 inputs over 3 channels need ceil(N/64)(ceil(N/64)+1)/2 * 3 =
+    3.08e9 loss partials, past 2^31: the count is kept in 64 bits, so the
+    allocation-free entry point rejects it on the host (its fixed scratch holds
+    65,536) and the allocating one rejects a channel count past the grid's
+    65,535; neither enqueues anything, so dummy pointers are never read."""
+    L = A.lib()
+    dummy = ctypes.c_void_p(16)
+    loss = ctypes.c_void_p(32)
+    fn = getattr(L, entry)
+    if entry == "acf_gain_forward_noalloc":
+        assert fn(dummy, dummy, dummy, 2_900_000, 3, loss, None, None) == A.EINVAL
+        assert fn(dummy, dummy, dummy, 64, 65_536, loss, None, None) == A.EINVAL
+    else:
+        assert fn(dummy, dummy, dummy, 64, 65_536, loss, None, None) == A.EINVAL

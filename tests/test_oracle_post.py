@@ -68,6 +68,30 @@ def test_channel_freqs_natural_order():
     assert np.allclose(f - F_SB, np.array([0, 1, 2, 3, -4, -3, -2, -1]) * FS / 8)
 
 
+@pytest.mark.parametrize("nu", [0.0, 0.37 * FS, -0.21 * FS])
+def test_raw_subband_delay_compensation_at_subband_centre(nu):
+    """A raw subband (one channel, no filter bank) is compensated at the
+    subband centre frequency (Sec. 4.2.4).  Inputs delayed by fractional
+    samples carry a baseband tone nu: x_i[t] = e^{2 pi i nu (t/fs - d_i)}
+    e^{-2 pi i f_sb d_i}, so the raw pair sums carry -2 pi (f_sb + nu)
+    (d_i - d_j), and compensation at f_sb must leave exactly -2 pi nu (d_i - d_j)
+    (zero for a tone at the centre).  A channel placed one sample rate away
+    (f_sb - fs) would leave 2 pi fs (d_i - d_j), which fractional delays make
+    visible."""
+    N, S = 5, 64
+    d = np.array([0.0, 0.31, 1.7, 4.05, 9.9]) / FS
+    t = np.arange(S) / FS
+    x = np.exp(2j * np.pi * nu * (t[:, None] - d[None, :])) * np.exp(-2j * np.pi * F_SB * d[None, :])
+    V = oracle.correlate(x.T[None])[None]                          # [1, 1, NB], raw subband
+    assert np.allclose(post.channel_freqs([F_SB], FS, 1), [[F_SB]], rtol=0, atol=0)
+    out = post.delay_compensate(V, d, [F_SB], FS)[0, 0]
+    i, j = post.pairs(N)
+    want = S * np.exp(-2j * np.pi * nu * (d[i] - d[j]))
+    assert np.allclose(out, want, rtol=0, atol=1e-9 * S)
+    if nu == 0.0:
+        assert np.max(np.abs(out.imag)) < 1e-9 * S
+
+
 def test_integrate_channels_against_reshape_sum():
     rng = np.random.default_rng(2)
     V = rng.normal(size=(3, 16, 10)) + 1j * rng.normal(size=(3, 16, 10))

@@ -1,18 +1,23 @@
-"""The allocation-free gain entry point (acf_gain_forward_noalloc) against the
-regular one, through the C ABI.
+"""The allocation-free gain entry point (acf_gain_forward_noalloc) through the
+C ABI, against the regular entry point and against the fp64 oracle.
 
-Some callers cannot allocate device memory while they run (work recorded in
-a CUDA-graph capture, processes with a fixed memory reservation, plug-ins that
-must not touch the allocator); this entry point keeps its loss partials in a
-fixed array compiled into the library.  The test calls it twice in a row --
-the second call sees the array holding the first call's contents -- and checks
-both results against acf_gain_forward within the gain tests' tolerance.  It
-sits in its own file so that pytest collects it last."""
+Some callers cannot allocate device memory while they run (processes whose
+device memory is reserved up front, real-time loops that must not block in
+the allocator, plug-ins of a framework that owns every allocation); this entry
+point keeps its loss partials in a fixed array compiled into the library.  The
+test makes two calls in a row on different problem sizes (small, then large,
+so the second call reads partials past the range the first one wrote) and
+checks each result against acf_gain_forward within the gain tests' tolerance
+and against oracle.gain_loss_grad; the second call must leave the device's
+free memory unchanged.  It sits in its own file so that pytest collects it
+last."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +42,7 @@ def test_noalloc_gain_matches_allocating_entry_point():
     L = A.lib()
     t = lambda a: torch.as_tensor(a, dtype=torch.complex64, device="cuda").contiguous()
     s = A.stream_handle()
-    for call, (N, C) in enumerate([(200, 8), (96, 3)]):        # two calls in a row, different sizes
+    for call, (N, C) in enumerate([(96, 3), (200, 8)]):        # two calls in a row: 18, then 80 partials
         R, V, g = _problem(N, C, 80 + call)
         Rt, Vt, gt = t(R), t(V), t(g)
         loss_a = torch.empty((), dtype=torch.float32, device="cuda")
@@ -45,13 +50,23 @@ def test_noalloc_gain_matches_allocating_entry_point():
         grad_a = torch.empty(N, dtype=torch.complex64, device="cuda")
         grad_b = torch.empty(N, dtype=torch.complex64, device="cuda")
         assert L.acf_gain_forward(A.ptr(Rt), A.ptr(Vt), A.ptr(gt), N, C, A.ptr(loss_a), A.ptr(grad_a), s) == A.OK
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert L.acf_gain_forward_noalloc(A.ptr(Rt), A.ptr(Vt), A.ptr(gt), N, C, A.ptr(loss_b), A.ptr(grad_b),
                                           s) == A.OK
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
         la, lb = loss_a.item(), loss_b.item()
         assert abs(la - lb) <= 1e-5 * abs(la)
         ga, gb = grad_a.cpu().numpy(), grad_b.cpu().numpy()
         assert np.max(np.abs(ga - gb)) <= 1e-4 * np.max(np.abs(ga))
+        # against the fp64 oracle, on the fp32 inputs the device saw
+        Lr, gref = oracle.gain_loss_grad(Rt.cpu().numpy().astype(np.complex128),
+                                         Vt.cpu().numpy().astype(np.complex128),
+                                         gt.cpu().numpy().astype(np.complex128))
+        assert abs(lb - Lr) <= 1e-4 * Lr
+        assert np.linalg.norm(gb - gref) <= 1e-4 * np.linalg.norm(gref)
 
 
 def test_noalloc_rejects_problems_beyond_the_fixed_scratch():
