@@ -46,6 +46,24 @@ bool chan_fast_supported(acf_in_dtype dt, int C, int P);
 cudaError_t launch_chan_fast(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
                              int n_sb, int N, int C, const float *h, const float *bp, const float2 *tw, int out_kind,
                              void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
+// Warp-specialised 64-channel, 16-tap channeliser (chan_ws.cu): ci8 / ci16
+// input read through a TMA tensor map (N a multiple of 16 bytes' worth of
+// inputs, 16-byte aligned samples).  It produces spectra
+// [chan_ws_first_spectrum(n_hist), roundup(T, 64)); the spectra before that
+// reach into the history and are left to the generic kernel.
+bool chan_ws_supported(acf_in_dtype dt, int C, int P, int N, const void *samples, long n_samples);
+long chan_ws_first_spectrum(long n_hist);
+cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf_in_dtype dt, int n_sb, int N,
+                           const float *h, const float *bp, float scale, int out_kind, void *out, void *out_lo,
+                           long t_stride, long T, cudaStream_t s);
+// Generic kernel restricted to spectra [0, m_head) (m_head a multiple of 16).
+cudaError_t launch_channelise_head(const void *hist, long n_hist, const void *samples, long n_samples,
+                                   acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
+                                   const float *bandpass, const float2 *tw, int out_kind, void *out,
+                                   void *out_lo, long t_stride, float scale, long T, long m_head, cudaStream_t s);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (NULL when
+// unavailable); returned untyped so this header needs no driver types.
+void *tensor_map_encoder();
 cudaError_t launch_transpose_raw(const void *samples, long n_samples, acf_in_dtype dt, int n_sb,
                                  int N, int out_kind, void *out, void *out_lo, long t_stride,
                                  float scale, cudaStream_t s);

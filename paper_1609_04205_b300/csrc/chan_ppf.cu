@@ -12,6 +12,8 @@
 //      radix-2 DIF across the warp with shuffles (L = min(C, 32));
 //   4. applies w_c, converts (fp32 / fp16 / fp16 hi+lo) and stores each
 //      output row (channel, input, re|im) as MS consecutive spectra.
+#include <algorithm>
+
 #include "acf_internal.h"
 
 namespace acf {
@@ -314,9 +316,9 @@ __global__ void k_history(const E *__restrict__ hist, long n_hist, const E *__re
 template <int C, int MS, int NI, typename IN>
 cudaError_t launch_t(const void *hist, long n_hist, const void *samples, long n_samples, int n_sb,
                      int N, int P, const float *h, const float *bp, const float2 *tw, int out_kind,
-                     void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
+                     void *out, void *out_lo, long t_stride, float scale, long T, long m_head, cudaStream_t s)
 {
-    const long T64 = round_up(T, 64);
+    long T64 = round_up(T, 64);
     if (T64 == 0) return cudaSuccess;
     // Every batch re-stages its own FIR windows, so a shorter time segment per
     // block costs nothing extra: halve it until the grid fills the GPU.
@@ -326,6 +328,12 @@ cudaError_t launch_t(const void *hist, long n_hist, const void *samples, long n_
     const long groups = (N + NI - 1) / NI;
     long m_per_block = 256;
     while (m_per_block > MS && groups * n_sb * ((T64 + m_per_block - 1) / m_per_block) < 4L * sms) m_per_block /= 2;
+    if (m_head > 0) {
+        // only spectra [0, m_head): one segment per block, m_head a multiple of MS
+        if (m_head % MS != 0) return cudaErrorInvalidValue;
+        m_per_block = m_head;
+        T64 = std::min(T64, m_head);
+    }
     const size_t smem = C * sizeof(float2) + (size_t)NI * MS * C * sizeof(float2) +
                         (size_t)(MS + P - 1) * C * NI * sizeof(IN);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -344,13 +352,13 @@ template <typename IN>
 cudaError_t launch_by_c(int C, const void *hist, long n_hist, const void *samples, long n_samples,
                         int n_sb, int N, int P, const float *h, const float *bp, const float2 *tw,
                         int out_kind, void *out, void *out_lo, long t_stride, float scale, long T,
-                        cudaStream_t s)
+                        long m_head, cudaStream_t s)
 {
     constexpr int NI = sizeof(IN) == 8 ? 2 : 4;
     switch (C) {
-    case 16:  return launch_t<16, 32, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, s);
-    case 64:  return launch_t<64, 16, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, s);
-    case 256: return launch_t<256, 8, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, s);
+    case 16:  return launch_t<16, 32, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
+    case 64:  return launch_t<64, 16, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
+    case 256: return launch_t<256, 8, NI, IN>(hist, n_hist, samples, n_samples, n_sb, N, P, h, bp, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
     default:  return cudaErrorInvalidValue;
     }
 }
@@ -375,6 +383,18 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
                               const float *bandpass, const float2 *tw, int out_kind, void *out,
                               void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
 {
+    if (chan_ws_supported(dt, C, P, N, samples, n_samples)) {
+        // spectra whose windows reach into the history: generic kernel; the
+        // rest (all of them after the first 16 of a push): warp-specialised kernel
+        const long m_head = std::min(chan_ws_first_spectrum(n_hist), round_up(T, 64));
+        cudaError_t e = cudaSuccess;
+        if (m_head > 0)
+            e = launch_channelise_head(hist, n_hist, samples, n_samples, dt, n_sb, N, C, P, h, bandpass, tw, out_kind,
+                                       out, out_lo, t_stride, scale, T, m_head, s);
+        if (e != cudaSuccess) return e;
+        return launch_chan_ws(samples, n_samples, n_hist, dt, n_sb, N, h, bandpass, scale, out_kind, out, out_lo,
+                              t_stride, T, s);
+    }
     if (chan_fast_supported(dt, C, P))
         return launch_chan_fast(hist, n_hist, samples, n_samples, dt, n_sb, N, C, h, bandpass, tw, out_kind, out,
                                 out_lo, t_stride, scale, T, s);
@@ -382,17 +402,26 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
                                      out, out_lo, t_stride, scale, T, s);
 }
 
+cudaError_t launch_channelise_head(const void *hist, long n_hist, const void *samples, long n_samples,
+                                   acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
+                                   const float *bandpass, const float2 *tw, int out_kind, void *out,
+                                   void *out_lo, long t_stride, float scale, long T, long m_head, cudaStream_t s)
+{
+    switch (dt) {
+    case ACF_IN_CI8:  return launch_by_c<char2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
+    case ACF_IN_CI16: return launch_by_c<short2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
+    case ACF_IN_CF32: return launch_by_c<float2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, m_head, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_channelise_generic(const void *hist, long n_hist, const void *samples, long n_samples,
                                       acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
                                       const float *bandpass, const float2 *tw, int out_kind, void *out,
                                       void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
 {
-    switch (dt) {
-    case ACF_IN_CI8:  return launch_by_c<char2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, s);
-    case ACF_IN_CI16: return launch_by_c<short2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, s);
-    case ACF_IN_CF32: return launch_by_c<float2>(C, hist, n_hist, samples, n_samples, n_sb, N, P, h, bandpass, tw, out_kind, out, out_lo, t_stride, scale, T, s);
-    }
-    return cudaErrorInvalidValue;
+    return launch_channelise_head(hist, n_hist, samples, n_samples, dt, n_sb, N, C, P, h, bandpass, tw, out_kind, out,
+                                  out_lo, t_stride, scale, T, 0, s);
 }
 
 cudaError_t launch_transpose_raw(const void *samples, long n_samples, acf_in_dtype dt, int n_sb,

@@ -1,0 +1,586 @@
+// Warp-specialised polyphase channeliser for the production geometry: 16
+// taps, 64 channels, complex int16 or int8 input (Sec. 4.2.3 FIR + FFT,
+// Sec. 4.2.4 bandpass + transpose into the X-engine operand layout).
+//
+// A persistent CTA (one per SM) walks a list of items; an item is NI
+// consecutive inputs (one 16-byte row of samples: 4 ci16 or 8 ci8) of one
+// subband over a segment of spectra.  Three roles share the CTA:
+//   * producer (FIR thread 0): TMA copies of [1024 time rows][NI inputs]
+//     tiles into a ring of shared-memory stages, one stage per batch of 16
+//     spectra (rows (m0 + 15) * 64 .. (m0 + 31) * 64: the newest sample of
+//     every phase of every spectrum in the batch) plus one prologue stage per
+//     item (the first 15 window rows);
+//   * 8 FIR warps: thread (input pair or input, phase n) keeps its 16 taps
+//     and the newest 16 samples of its phase in registers, so every input
+//     sample is read from shared memory once and costs 16 packed fp32x2 FMAs
+//     (Sec. 4.2.3's FIR held in registers); the FIR outputs y_m[n] of a batch
+//     go to one of two Y buffers;
+//   * 4 FFT warps, two groups of two, one group per Y buffer: thread
+//     (input, spectrum) reads its 64 FIR outputs and computes the whole
+//     64-point DFT in registers as radix 8 x 8 with compile-time twiddles, no
+//     shared-memory pass between the radix stages; then the bandpass weight
+//     times the output scale (Sec. 4.2.4), the conversion, and the store:
+//     lanes hold consecutive spectra, so neighbouring lanes swap one word and
+//     each writes a time-contiguous pair of one output row (the transpose of
+//     Sec. 4.2.4 done in registers).
+// The FIR warps and the FFT groups hand batches over through mbarriers; every
+// wait is bounded (about one second of SM clock), after which the CTA sets the
+// device error word, stops, and lets its TMA copies land before exiting.
+// Spectra whose windows reach into the filter history (the first
+// ceil(n_hist / 64), rounded up to 16, of a push) are left to the generic
+// kernel: this one reads only the pushed samples, through one tensor map.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "acf_internal.h"
+
+namespace acf {
+namespace {
+
+constexpr int kC = 64;                  // channels
+constexpr int kP = 16;                  // taps
+constexpr int kMB = 16;                 // spectra per batch (== taps: window slots stay static)
+constexpr int kFirWarps = 8;
+constexpr int kFftWarps = 4;            // two groups of two
+constexpr int kThreadsWs = 32 * (kFirWarps + kFftWarps);
+constexpr int kFirThreads = 32 * kFirWarps;
+constexpr int kFftGroup = 64;           // threads per FFT group
+constexpr int kRowsPerStage = kMB * kC; // 1024 time rows, 16 bytes each
+constexpr int kStageBytes = kRowsPerStage * 16;
+constexpr int kBoxRows = 256;
+constexpr int kYRow = kC * 8 + 16;      // one spectrum of one input: 64 complex + 16 B
+constexpr long long kWaitCyclesWs = 1LL << 31;   // about one second of SM clock
+
+template <typename IN>
+struct WsGeo {
+    static constexpr int E = sizeof(IN);           // bytes per complex sample
+    static constexpr int NI = 16 / E;              // inputs per item (one 16-byte row)
+    static constexpr int IPT = NI / 4;             // inputs per FIR thread
+    static constexpr int STAGES = IPT == 1 ? 6 : 4;
+    // Y buffer: [NI][kMB spectra][kYRow]; the per-input stride keeps the FIR
+    // stores (lanes = 4 input slots x 8 phases) conflict-free, the 528-byte
+    // spectrum stride keeps the FFT's 16-byte reads (lanes = spectra) so.
+    static constexpr int SI = kMB * kYRow + 32 / IPT;
+    static constexpr int YBUF = NI * SI;
+    static constexpr int OFF_Y = STAGES * kStageBytes;
+    static constexpr int OFF_W = OFF_Y + 2 * YBUF;              // bandpass x scale, [k1][k2]
+    static constexpr int OFF_BAR = OFF_W + kC * 4;
+    static constexpr int NBAR = 2 * STAGES + 4;
+    static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;   // + alignment slack
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+struct WsParams {
+    CUtensorMap map;      // input [n_sb][n_samples][N] samples; boxes of NI inputs x 256 rows
+    const float *h;       // taps, h[k * 64 + n]
+    const float *bp;      // bandpass weights, 64
+    float osc;            // output scale (fp16 outputs) or 1
+    void *out, *out_lo;
+    long t_stride;
+    long row0;            // input row of stream row 0 (= -n_hist)
+    long m_begin, m_end;  // spectra handled, multiples of 16
+    long T;               // valid spectra: [T, m_end) are written as zeros
+    long seg;             // spectra per item, a multiple of 16
+    int groups, n_sb, n_items, N;
+    int *err;
+};
+
+// ---- small PTX helpers --------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_test(uint32_t b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `parity`: false after the CTA aborted or
+// about one second without progress (then it records `code` and aborts).
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int *abort_flag, int *err, int code) {
+    if (bar_test(b, parity)) return true;
+    const long long t0 = clock64();
+    for (int it = 1;; ++it) {
+        if (bar_test(b, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitCyclesWs) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z) : "memory");
+}
+// Shared-memory data accesses are plain C++ (the compiler schedules them
+// freely between the barrier waits, whose asm carries a memory clobber).
+__device__ __forceinline__ uint32_t lds32(const unsigned char *p) { return *reinterpret_cast<const uint32_t *>(p); }
+__device__ __forceinline__ float4 lds128(const unsigned char *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sts64(unsigned char *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+
+// ---- complex arithmetic on packed fp32x2 ------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }   // * (-i)
+
+// cos and sin of 2 pi k / n by Taylor series in double, evaluated by the
+// compiler (the twiddles below are compile-time constants).
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double t = 1.0, s = 1.0;
+    for (int i = 1; i < 30; ++i) {
+        t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double t = x, s = x;
+    for (int i = 1; i < 30; ++i) {
+        t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        s += t;
+    }
+    return s;
+}
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// a * W_64^K with W_64 = exp(-2 pi i / 64).
+template <int K>
+__device__ __forceinline__ float2 mul_w64(float2 a) {
+    constexpr int k = K & 63;
+    if constexpr (k == 0) {
+        return a;
+    } else if constexpr (k == 16) {
+        return make_float2(a.y, -a.x);
+    } else if constexpr (k == 32) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (k == 48) {
+        return make_float2(-a.y, a.x);
+    } else {
+        constexpr float c = (float)taylor_cos(kTwoPi * k / 64.0);
+        constexpr float s = (float)taylor_sin(kTwoPi * k / 64.0);
+        // (x + i y)(c - i s) = (x c + y s) + i (y c - x s)
+        return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -(a.x * s)));
+    }
+}
+
+// 8-point DFT in place, natural order: A[k] = sum_r a[r] exp(-2 pi i r k / 8)
+// (radix-2 decimation in frequency, outputs placed back in natural order).
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+    constexpr float r2 = 0.70710678118654752440f;
+    const float2 b0 = cadd(a[0], a[4]), b1 = cadd(a[1], a[5]), b2 = cadd(a[2], a[6]), b3 = cadd(a[3], a[7]);
+    const float2 d0 = csub(a[0], a[4]);
+    float2 d1 = csub(a[1], a[5]);
+    const float2 d2 = mul_mi(csub(a[2], a[6]));
+    float2 d3 = csub(a[3], a[7]);
+    d1 = make_float2(r2 * (d1.x + d1.y), r2 * (d1.y - d1.x));      // * W_8^1
+    d3 = make_float2(r2 * (d3.y - d3.x), -r2 * (d3.x + d3.y));     // * W_8^3
+    const float2 e0 = cadd(b0, b2), e1 = cadd(b1, b3), e2 = csub(b0, b2), e3 = mul_mi(csub(b1, b3));
+    const float2 f0 = cadd(d0, d2), f1 = cadd(d1, d3), f2 = csub(d0, d2), f3 = mul_mi(csub(d1, d3));
+    a[0] = cadd(e0, e1);
+    a[4] = csub(e0, e1);
+    a[2] = cadd(e2, e3);
+    a[6] = csub(e2, e3);
+    a[1] = cadd(f0, f1);
+    a[5] = csub(f0, f1);
+    a[3] = cadd(f2, f3);
+    a[7] = csub(f2, f3);
+}
+
+// Radix-8 pass 1 on column S (points S + 8 r): 8-point DFT over r, then the
+// twiddle W_64^(S k1); results back in place (slot S + 8 k1).
+template <int S>
+__device__ __forceinline__ void pass1(float2 (&z)[64]) {
+    float2 a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = z[S + 8 * r];
+    dft8(a);
+    z[S] = a[0];
+    z[S + 8] = mul_w64<S * 1>(a[1]);
+    z[S + 16] = mul_w64<S * 2>(a[2]);
+    z[S + 24] = mul_w64<S * 3>(a[3]);
+    z[S + 32] = mul_w64<S * 4>(a[4]);
+    z[S + 40] = mul_w64<S * 5>(a[5]);
+    z[S + 48] = mul_w64<S * 6>(a[6]);
+    z[S + 56] = mul_w64<S * 7>(a[7]);
+}
+
+template <typename IN, int IPT>
+__device__ __forceinline__ void unpack(uint32_t w, float2 (&x)[IPT]);
+template <>
+__device__ __forceinline__ void unpack<short2, 1>(uint32_t w, float2 (&x)[1]) {
+    x[0] = make_float2((float)(short)(w & 0xffffu), (float)(short)(w >> 16));
+}
+template <>
+__device__ __forceinline__ void unpack<char2, 2>(uint32_t w, float2 (&x)[2]) {
+    x[0] = make_float2((float)(signed char)(w & 0xffu), (float)(signed char)((w >> 8) & 0xffu));
+    x[1] = make_float2((float)(signed char)((w >> 16) & 0xffu), (float)(signed char)(w >> 24));
+}
+
+// FIR of one batch: 16 outputs per (input, phase); spectra at or past T
+// (MASK) are written as zeros so their DFT is exactly zero.
+template <typename IN, int IPT, bool MASK>
+__device__ __forceinline__ void fir_batch(const float2 (&hr)[kP], float2 (&win)[IPT][kP], const unsigned char *xs,
+                                          unsigned char *ys, int ip, int n, long m0, long T)
+{
+    using G = WsGeo<IN>;
+#pragma unroll
+    for (int mm = 0; mm < kMB; ++mm) {
+        float2 xv[IPT];
+        unpack<IN, IPT>(lds32(xs + (mm * kC + n) * 16 + ip * 4), xv);
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) {
+            win[u][(mm + kP - 1) % kP] = xv[u];
+            float2 acc = __fmul2_rn(hr[0], win[u][mm % kP]);
+#pragma unroll
+            for (int k = 1; k < kP; ++k) acc = __ffma2_rn(hr[k], win[u][(mm + k) % kP], acc);
+            if (MASK && m0 + mm >= T) acc = make_float2(0.f, 0.f);
+            sts64(ys + (ip * IPT + u) * G::SI + mm * kYRow + n * 8, acc);
+        }
+    }
+}
+
+// Store one channel value of this lane's spectrum: neighbouring lanes hold
+// spectra m (even) and m + 1 (odd); the even lane writes the real row's pair,
+// the odd lane the imaginary row's pair, at column m.
+template <int OUTK>
+__device__ __forceinline__ void put(float2 v, float w, bool odd, uint32_t sel, void *out, void *out_lo, long off,
+                                    bool ok)
+{
+    const float re = v.x * w, im = v.y * w;
+    if constexpr (OUTK == OUT_F32) {
+        const float recv = __shfl_xor_sync(0xffffffffu, odd ? re : im, 1);
+        const float2 o = odd ? make_float2(recv, im) : make_float2(re, recv);
+        if (ok) *reinterpret_cast<float2 *>(static_cast<float *>(out) + off) = o;
+    } else {
+        const __half2 hv = __floats2half2_rn(re, im);
+        uint32_t hb;
+        memcpy(&hb, &hv, 4);
+        const uint32_t pb = __shfl_xor_sync(0xffffffffu, hb, 1);
+        if (ok) *reinterpret_cast<uint32_t *>(static_cast<__half *>(out) + off) = __byte_perm(hb, pb, sel);
+        if constexpr (OUTK == OUT_F16X3) {
+            const float2 f = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(re - f.x, im - f.y);
+            uint32_t lb;
+            memcpy(&lb, &lv, 4);
+            const uint32_t pl = __shfl_xor_sync(0xffffffffu, lb, 1);
+            if (ok) *reinterpret_cast<uint32_t *>(static_cast<__half *>(out_lo) + off) = __byte_perm(lb, pl, sel);
+        }
+    }
+}
+
+struct ItemPos {
+    int sb, grp;
+    long m_lo, m_hi;
+};
+__device__ __forceinline__ ItemPos decode_item(const WsParams &P, int item) {
+    ItemPos d;
+    const int seg = item / (P.n_sb * P.groups);
+    const int rem = item - seg * (P.n_sb * P.groups);
+    d.sb = rem / P.groups;
+    d.grp = rem - d.sb * P.groups;
+    d.m_lo = P.m_begin + (long)seg * P.seg;
+    d.m_hi = min(P.m_end, d.m_lo + P.seg);
+    return d;
+}
+
+template <typename IN, int OUTK>
+__global__ void __launch_bounds__(kThreadsWs, 1) k_ppf64_ws(const __grid_constant__ WsParams P)
+{
+    using G = WsGeo<IN>;
+    constexpr int NI = G::NI, IPT = G::IPT, NS = G::STAGES;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ int abort_flag;
+    const uint32_t s0 = su32(smem);
+    const uint32_t bar0 = s0 + G::OFF_BAR;
+    auto xfull = [&](int s) { return bar0 + 8u * s; };
+    auto xempty = [&](int s) { return bar0 + 8u * (NS + s); };
+    auto yfull = [&](int b) { return bar0 + 8u * (2 * NS + b); };
+    auto yempty = [&](int b) { return bar0 + 8u * (2 * NS + 2 + b); };
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NS; ++s) {
+            bar_init(xfull(s), 1);
+            bar_init(xempty(s), kFirThreads);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(yfull(b), kFirThreads);
+            bar_init(yempty(b), kFftGroup);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.map)) : "memory");
+    }
+    if (tid >= kFirThreads && tid < kFirThreads + kC) {
+        // bandpass x scale, stored [k1][k2] for channel c = k1 + 8 k2
+        const int c = tid - kFirThreads;
+        reinterpret_cast<float *>(smem + G::OFF_W)[(c & 7) * 8 + (c >> 3)] = __ldg(P.bp + c) * P.osc;
+    }
+    __syncthreads();
+
+    if (warp < kFirWarps) {
+        // ---------------- FIR warps (thread 0 also produces) ----------------
+        const int fi = tid, ip = fi & 3, n = fi >> 2;
+        float2 hr[kP];
+#pragma unroll
+        for (int k = 0; k < kP; ++k) {
+            const float hv = __ldg(P.h + k * kC + n);
+            hr[k] = make_float2(hv, hv);
+        }
+        float2 win[IPT][kP];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int k = 0; k < kP; ++k) win[u][k] = make_float2(0.f, 0.f);
+        // producer state (thread 0): the next load to issue
+        long issued = 0;
+        int p_item = blockIdx.x, p_j = 0;
+        ItemPos pd = decode_item(P, p_item < P.n_items ? p_item : 0);
+        bool p_done = p_item >= P.n_items;
+        auto produce = [&](long upto) -> bool {   // issue loads [issued, upto)
+            while (!p_done && issued < upto) {
+                const int s = (int)(issued % NS);
+                if (issued >= NS && !bar_wait(xempty(s), (uint32_t)(((issued / NS) - 1) & 1), &abort_flag, P.err, 21))
+                    return false;
+                const long srow = p_j == 0 ? pd.m_lo * kC : (pd.m_lo + (long)kMB * (p_j - 1) + (kP - 1)) * kC;
+                const long y = srow + P.row0;
+                bar_expect(xfull(s), kStageBytes);
+#pragma unroll
+                for (int q = 0; q < kRowsPerStage / kBoxRows; ++q)
+                    tma_3d(s0 + s * kStageBytes + q * kBoxRows * 16, &P.map, xfull(s), pd.grp * NI,
+                           (int)(y + q * kBoxRows), pd.sb);
+                ++issued;
+                const long nb = (pd.m_hi - pd.m_lo) / kMB;
+                if (++p_j > nb) {
+                    p_j = 0;
+                    p_item += gridDim.x;
+                    if (p_item >= P.n_items) p_done = true;
+                    else pd = decode_item(P, p_item);
+                }
+            }
+            return true;
+        };
+        long L = 0, gbat = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const ItemPos d = decode_item(P, item);
+            // prologue: window rows 0 .. 14 of the item's first spectrum
+            if (fi == 0) ok = produce(L + NS);
+            if (ok) ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 22);
+            if (!ok) break;
+            {
+                const unsigned char *xs = smem + (L % NS) * kStageBytes;
+#pragma unroll
+                for (int k = 0; k < kP - 1; ++k) {
+                    float2 xv[IPT];
+                    unpack<IN, IPT>(lds32(xs + (k * kC + n) * 16 + ip * 4), xv);
+#pragma unroll
+                    for (int u = 0; u < IPT; ++u) win[u][k] = xv[u];
+                }
+                bar_arrive(xempty((int)(L % NS)));
+                ++L;
+            }
+            for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++gbat) {
+                if (fi == 0) ok = produce(L + NS);
+                const int yb = (int)(gbat & 1);
+                if (ok && gbat >= 2)
+                    ok = bar_wait(yempty(yb), (uint32_t)(((gbat >> 1) - 1) & 1), &abort_flag, P.err, 23);
+                if (ok) ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 24);
+                if (!ok) break;
+                const unsigned char *xs = smem + (L % NS) * kStageBytes;
+                unsigned char *ys = smem + G::OFF_Y + yb * G::YBUF;
+                if (m0 + kMB <= P.T) fir_batch<IN, IPT, false>(hr, win, xs, ys, ip, n, m0, P.T);
+                else fir_batch<IN, IPT, true>(hr, win, xs, ys, ip, n, m0, P.T);
+                bar_arrive(xempty((int)(L % NS)));
+                bar_arrive(yfull(yb));
+                ++L;
+            }
+        }
+        if (fi == 0) {
+            // let every copy this CTA issued land before it exits (all were
+            // consumed unless the CTA aborted)
+            for (long q = issued - 1; q >= 0 && q >= issued - NS; --q) {
+                const int s = (int)(q % NS);
+                for (long long it = 0; it < (1LL << 22) && !bar_test(xfull(s), (uint32_t)((q / NS) & 1)); ++it)
+                    __nanosleep(256);
+            }
+        }
+    } else {
+        // ---------------- FFT warps ----------------
+        const int ft = tid - kFirThreads, g = ft >> 6, tt = ft & 63;
+        const bool odd = (tt & 1) != 0;
+        const uint32_t sel = odd ? 0x3276u : 0x5410u;
+        const unsigned char *wsm = smem + G::OFF_W;
+        const long cstride = 2L * P.N * P.t_stride;          // elements between channels
+        long gbat = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const ItemPos d = decode_item(P, item);
+            for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++gbat) {
+                if ((int)(gbat & 1) != g) continue;
+                ok = bar_wait(yfull(g), (uint32_t)((gbat >> 1) & 1), &abort_flag, P.err, 25);
+                if (!ok) break;
+                const unsigned char *ys = smem + G::OFF_Y + g * G::YBUF;
+#pragma unroll 1
+                for (int q = 0; q < IPT; ++q) {
+                    const int job = tt + kFftGroup * q;
+                    const int i = job >> 4, mm = job & 15;
+                    float2 z[64];
+                    const unsigned char *yr = ys + i * G::SI + mm * kYRow;
+#pragma unroll
+                    for (int p = 0; p < 32; ++p) {
+                        const float4 v = lds128(yr + 16 * p);
+                        z[2 * p] = make_float2(v.x, v.y);
+                        z[2 * p + 1] = make_float2(v.z, v.w);
+                    }
+                    if (q == IPT - 1) bar_arrive(yempty(g));
+                    pass1<0>(z); pass1<1>(z); pass1<2>(z); pass1<3>(z);
+                    pass1<4>(z); pass1<5>(z); pass1<6>(z); pass1<7>(z);
+                    const int nn = d.grp * NI + i;
+                    const bool st = nn < P.N;
+                    const long off = ((long)d.sb * kC * 2 * P.N + 2L * nn + (odd ? 1 : 0)) * P.t_stride + m0 + (mm & ~1);
+#pragma unroll
+                    for (int k1 = 0; k1 < 8; ++k1) {
+                        float2 a[8];
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) a[s] = z[s + 8 * k1];
+                        dft8(a);
+                        const float4 w0 = lds128(wsm + 32 * k1), w1 = lds128(wsm + 32 * k1 + 16);
+                        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int k2 = 0; k2 < 8; ++k2)
+                            put<OUTK>(a[k2], wv[k2], odd, sel, P.out, P.out_lo, off + (long)(k1 + 8 * k2) * cstride, st);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename IN, int OUTK>
+cudaError_t launch_ws_t(WsParams &P, int grid, cudaStream_t s)
+{
+    using G = WsGeo<IN>;
+    auto kern = k_ppf64_ws<IN, OUTK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreadsWs, G::SMEM, s>>>(P);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool chan_ws_supported(acf_in_dtype dt, int C, int P, int N, const void *samples, long n_samples)
+{
+    if (C != kC || P != kP || (dt != ACF_IN_CI8 && dt != ACF_IN_CI16)) return false;
+    if (n_samples < kBoxRows || n_samples > 0x7fffffffL) return false;   // a box never exceeds the rows
+    const int ni = dt == ACF_IN_CI16 ? 4 : 8;
+    return N % ni == 0 && reinterpret_cast<uintptr_t>(samples) % 16 == 0 && tensor_map_encoder() != nullptr;
+}
+
+long chan_ws_first_spectrum(long n_hist)
+{
+    // first spectrum whose window starts inside the pushed samples, rounded up to a batch
+    return round_up((n_hist + kC - 1) / kC, kMB);
+}
+
+cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf_in_dtype dt, int n_sb, int N,
+                           const float *h, const float *bp, float scale, int out_kind, void *out, void *out_lo,
+                           long t_stride, long T, cudaStream_t s)
+{
+    const long m_begin = chan_ws_first_spectrum(n_hist);
+    const long m_end = round_up(T, 64);
+    if (m_end <= m_begin) return cudaSuccess;
+    const int E = in_elem_bytes(dt), NI = 16 / E;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!enc) return cudaErrorNotSupported;
+    WsParams P;
+    std::memset(&P, 0, sizeof(P));
+    cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)n_samples, (cuuint64_t)n_sb};
+    cuuint64_t strides[2] = {(cuuint64_t)N * E, (cuuint64_t)n_samples * N * E};
+    cuuint32_t box[3] = {(cuuint32_t)NI, (cuuint32_t)kBoxRows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&P.map, E == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                     const_cast<void *>(samples), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    P.h = h;
+    P.bp = bp;
+    P.osc = out_kind == OUT_F32 ? 1.f : scale;
+    P.out = out;
+    P.out_lo = out_lo;
+    P.t_stride = t_stride;
+    P.row0 = -n_hist;
+    P.m_begin = m_begin;
+    P.m_end = m_end;
+    P.T = T;
+    P.groups = (N + NI - 1) / NI;
+    P.n_sb = n_sb;
+    P.N = N;
+    P.err = device_error_word();
+    if (!P.err) return cudaErrorMemoryAllocation;
+    // split each (subband, input group) into nseg time segments: the fewest
+    // whose per-CTA load count (items per CTA x loads per item, prologue
+    // included) is smallest
+    const long nbat = (m_end - m_begin) / kMB;
+    const long pairs = (long)n_sb * P.groups;
+    long best = -1, best_cost = 0;
+    for (long ns = 1; ns <= 8 && ns <= nbat; ++ns) {
+        const long segb = (nbat + ns - 1) / ns;
+        const long items = pairs * ((nbat + segb - 1) / segb);
+        const long grid = std::min<long>(items, sms);
+        const long cost = (items + grid - 1) / grid * (segb + 1);
+        if (best < 0 || cost < best_cost) {
+            best = segb;
+            best_cost = cost;
+        }
+    }
+    P.seg = best * kMB;
+    const long nseg = (nbat + best - 1) / best;
+    const long items = pairs * nseg;
+    if (items > 0x7fffffffL) return cudaErrorInvalidValue;
+    P.n_items = (int)items;
+    const int grid = (int)std::min<long>(items, sms);
+    if (dt == ACF_IN_CI16) {
+        switch (out_kind) {
+        case OUT_F32: return launch_ws_t<short2, OUT_F32>(P, grid, s);
+        case OUT_F16: return launch_ws_t<short2, OUT_F16>(P, grid, s);
+        default: return launch_ws_t<short2, OUT_F16X3>(P, grid, s);
+        }
+    }
+    switch (out_kind) {
+    case OUT_F32: return launch_ws_t<char2, OUT_F32>(P, grid, s);
+    case OUT_F16: return launch_ws_t<char2, OUT_F16>(P, grid, s);
+    default: return launch_ws_t<char2, OUT_F16X3>(P, grid, s);
+    }
+}
+
+}  // namespace acf

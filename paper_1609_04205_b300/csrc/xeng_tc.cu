@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "acf_internal.h"
@@ -804,18 +805,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+}
+
+}  // namespace
+
+void *tensor_map_encoder()
+{
+    static void *fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+            fn = p;
+    });
     return fn;
 }
-
-}  // namespace
 
 struct TcPlan {
     TcParams params;

@@ -71,6 +71,88 @@ def test_channelise_fp16_split_reconstructs():
     assert err <= 1e-6 * ref.abs().max().item() * 4
 
 
+@pytest.mark.parametrize("dtype,N", [("ci16", 36), ("ci8", 40)])
+@pytest.mark.parametrize("n_hist", [0, 500, 1023, 3000])
+def test_channelise_64ch_history_and_segments_vs_oracle(dtype, N, n_hist):
+    """The warp-specialised 64-channel path (N a multiple of one 16-byte row
+    of inputs): spectra whose windows reach into the history come from the
+    generic kernel, the rest from the TMA-fed kernel, split into several time
+    segments per (subband, input group); two subbands; f32 output against the
+    oracle on the concatenated stream, zeroed tail."""
+    _dev()
+    C, P, S, n_sb = 64, 16, 64 * 700 + 37, 2
+    sig = 512.0 if dtype == "ci16" else 16.0
+    full = _samples(N, n_hist + S, n_sb, dtype, sigma=sig, seed=60 + n_hist)
+    hist = full[:, :n_hist].contiguous() if n_hist else None
+    x = full[:, n_hist:].contiguous()
+    X, _, T = acf.channelise(x, C, P, out_kind="f32", hist=hist)
+    torch.cuda.synchronize()
+    assert T == oracle.n_spectra(n_hist + S, P, C)
+    h = oracle.prototype(P, C)
+    for sb in range(n_sb):
+        ref = oracle.channelise(full[sb].cpu().numpy(), h, P, C)
+        got = X[sb].cpu().numpy().astype(np.float64)
+        gc = got[:, 0::2, :T] + 1j * got[:, 1::2, :T]
+        assert np.max(np.abs(gc - ref)) <= 2e-6 * np.max(np.abs(ref))
+        assert np.all(got[:, :, T:(T + 63) // 64 * 64] == 0)
+
+
+@pytest.mark.parametrize("dtype,N", [("ci16", 48), ("ci8", 64)])
+def test_channelise_64ch_fp16_outputs_and_bandpass(dtype, N):
+    """fp16 and split fp16 outputs of the 64-channel path with non-uniform
+    bandpass weights and an output scale: hi is the fp16 rounding of the
+    scaled fp32 value and hi + lo reconstructs it to fp32 accuracy."""
+    _dev()
+    C, P, S = 64, 16, 64 * 300 + 5
+    sig = 512.0 if dtype == "ci16" else 16.0
+    x = _samples(N, S, 2, dtype, sigma=sig, seed=70)
+    w = synth.bandpass_ripple(C, 9)
+    sc = 0.25 if dtype == "ci16" else 4.0
+    X32, _, T = acf.channelise(x, C, P, out_kind="f32", bandpass=w)
+    Xh, _, _ = acf.channelise(x, C, P, out_kind="f16", bandpass=w, scale=sc)
+    Xh3, Xl3, _ = acf.channelise(x, C, P, out_kind="f16x3", bandpass=w, scale=sc)
+    torch.cuda.synchronize()
+    ref = oracle.channelise(x[0].cpu().numpy(), oracle.prototype(P, C), P, C, bandpass=w.astype(np.float64))
+    got = X32[0].cpu().numpy().astype(np.float64)
+    gc = got[:, 0::2, :T] + 1j * got[:, 1::2, :T]
+    assert np.max(np.abs(gc - ref)) <= 2e-6 * np.max(np.abs(ref))
+    v = (X32 * sc)[..., :T]
+    assert torch.equal(Xh[..., :T], Xh3[..., :T])
+    # fp16 rounding of the scaled value: within half an fp16 ulp of it, up to fp32 noise
+    assert ((Xh[..., :T].float() - v).abs() <= v.abs() * 2.0 ** -11 + 1e-6 * v.abs().max()).all()
+    recon = Xh3[..., :T].float() + Xl3[..., :T].float()
+    assert (recon - v).abs().max().item() <= 4e-6 * v.abs().max().item()
+    assert (Xh[..., T:] == 0).all() and (Xl3[..., T:] == 0).all()
+
+
+def test_correlator_64ch_streaming_pushes_ci16():
+    """Context path over five ragged pushes (history carried by the generic
+    head of each push, the rest by the TMA-fed kernel), integrations of two
+    pushes, split FP16, against the oracle's stream partition."""
+    _dev()
+    N, C, P = 44, 64, 16
+    pushes = [5000, 1300, 64 * 40 + 7, 260, 9000]
+    S = sum(pushes)
+    sky = synth.make_sky(N, 2, (0.1, 0.4), 77)
+    x = synth.voltages(N, S, 2, "ci16", 512.0, sky, 77, device="cuda")
+    xs = x.cpu().numpy()
+    with acf.Correlator(N, 2, C, P, 2, "fp16x3", "ci16", max(pushes)) as c:
+        outs = []
+        t0 = 0
+        for n in pushes:
+            c.push(x[:, t0:t0 + n].contiguous())
+            t0 += n
+            V = c.visibilities()
+            if V is not None:
+                outs.append(V.clone())
+        assert len(outs) == 2
+    torch.cuda.synchronize()
+    for sb in range(2):
+        ref = oracle.correlator(xs[sb], P, C, push_sizes=pushes, n_integrate=2)
+        for k in range(2):
+            assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
+
+
 # ---------------------------------------------------------------- X-engines
 @pytest.mark.parametrize("N,T", [(1, 1), (3, 37), (64, 100), (97, 500), (130, 64)])
 def test_xengine_simt_vs_oracle(N, T):
