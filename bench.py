@@ -51,20 +51,17 @@ def fp32_fma_peak_tflops(torch, sm_max_mhz):
 
 def xeng_traffic_per_subband():
     """DRAM bytes per subband of the X-engine launch from the committed ncu
-    summary, valid only while the kernel source is the one that was captured
-    (one-subband capture, scaled by subbands: traffic grows in proportion)."""
+    capture (profiles/xeng_traffic.json), valid only while the kernel source
+    is the one that was captured (a one-subband capture, scaled by subbands:
+    subbands are independent problems, so traffic grows in proportion)."""
     import hashlib
-    import re
-    prof = os.path.join(ROOT, "profiles", "xeng_tc_chan64_fp16_a12_1subband.md")
-    src = os.path.join(ROOT, "paper_1609_04205_b300", "csrc", "xeng_tc.cu")
+    side = os.path.join(ROOT, "profiles", "xeng_traffic.json")
     try:
-        txt = open(prof).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        m = re.search(r"xeng_tc.cu sha256 prefix `([0-9a-f]+)`", txt)
-        t = re.search(r"traffic_per_subband_bytes k_xeng_tc2?: (\d+)", txt)
-        if m and t and m.group(1) == h:
-            return int(t.group(1))
-    except OSError:
+        d = json.load(open(side))
+        src = os.path.join(ROOT, d["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == d["source_sha256_16"]:
+            return int(d["traffic_per_subband_bytes"])
+    except (OSError, KeyError, ValueError):
         pass
     return None
 
@@ -115,29 +112,48 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
-def cpu_oracle_sample(seconds_hint=True):
+ACC_CHANS = [0, 17]          # channels of subband 0 the oracle leg computes
+INT8_ACC_INPUTS = 64         # inputs of A-6 subband 0 the exact integer oracle sums
+
+
+def cpu_oracle_sample(x0=None):
     """fp64 oracle on a bounded slice of the default workload: subband 0, two
-    channels, all 1152 inputs, one 1 s integration (195,313 samples)."""
+    channels, all 1152 inputs, one 1 s integration (195,313 samples).  x0 is
+    subband 0 of the benchmark's own input ([S, N, 2] int16, host), whose
+    steady-state push the oracle then reproduces; without it the slice is
+    drawn here.  Returns the timing and the oracle's V."""
     import numpy as np
 
     import oracle
     import synth
     w = synth.WORKLOADS["a12"]
     N, S = w["n_inputs"], w["n_samples"]
-    sky = synth.make_sky(N, w["n_sources"], w["flux"], w["seed"])
-    x = synth.voltages(N, S, 1, "ci16", w["sigma"], sky, w["seed"], device="cpu")[0].numpy()
+    given = x0 is not None
+    if x0 is None:
+        sky = synth.make_sky(N, w["n_sources"], w["flux"], w["seed"])
+        x0 = synth.voltages(N, S, 1, "ci16", w["sigma"], sky, w["seed"], device="cpu")[0].numpy()
     C, P = w["n_channels"], w["n_taps"]
-    chans = [0, 17]
-    t0 = time.perf_counter()
-    X = oracle.channelise(x, oracle.prototype(P, C), P, C, chans=chans)
+    h = oracle.prototype(P, C)
+    if given:
+        # the benchmark pushes the same one-second block every step, so every
+        # timed push is the second push of the stream x0 ++ x0: its spectra
+        # m in [T1, T2) start where the first push's T1 spectra stopped
+        T1 = oracle.n_spectra(S, P, C)
+        T2 = oracle.n_spectra(2 * S, P, C)
+        seg = np.concatenate([x0[T1 * C:], x0], axis=0)
+        t0 = time.perf_counter()
+        X = oracle.channelise(seg, h, P, C, m_begin=0, m_end=T2 - T1, chans=ACC_CHANS)
+    else:
+        t0 = time.perf_counter()
+        X = oracle.channelise(x0, h, P, C, chans=ACC_CHANS)
     V = oracle.correlate(X)
     dt = time.perf_counter() - t0
     T = X.shape[2]
-    ops = xops(N, T, len(chans), 1)
+    ops = xops(N, T, len(ACC_CHANS), 1)
     assert np.isfinite(V).all()
     return dict(value=ops / dt / 1e12, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
                 sample="A-12 workload, subband 0, channels {0, 17}, 1152 inputs, 1 s (3051 spectra); "
-                       "fp64 direct FIR + naive DFT + brute-force pairs, %.1f s" % dt, seconds=dt)
+                       "fp64 direct FIR + naive DFT + brute-force pairs, %.1f s" % dt, seconds=dt), V
 
 
 def run_reference(args):
@@ -150,7 +166,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_oracle_sample()
     for _ in range(args.steps):
-        vals.append(cpu_oracle_sample())
+        vals.append(cpu_oracle_sample()[0])
     v = statistics.median([r["value"] for r in vals])
     secs = sum(r["seconds"] for r in vals)
     line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
@@ -165,8 +181,20 @@ def run_reference(args):
     return 0
 
 
-def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
-    """Steps of the whole stage in one precision mode; returns dict with timings."""
+def norm_err(V, R, n):
+    """max |dV_ij| / sqrt(V_ii V_jj) of V against R ([channels, NB] complex)."""
+    import numpy as np
+    i = np.repeat(np.arange(n), np.arange(1, n + 1))
+    j = np.concatenate([np.arange(k + 1) for k in range(n)])
+    d = np.arange(n) * (np.arange(n) + 1) // 2 + np.arange(n)
+    auto = R[:, d].real
+    return float(np.max(np.abs(V - R) / np.sqrt(auto[:, i] * auto[:, j])))
+
+
+def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None, keep=None):
+    """Steps of the whole stage in one precision mode; returns dict with timings.
+    keep(out) -> host copy of the part of the last step's visibilities the
+    accuracy check compares with the oracle."""
     N, n_sb, C, P = w["n_inputs"], w["n_subbands"], w["n_channels"], w["n_taps"]
     S = w["n_samples"]
     c = acf.Correlator(N, n_sb, C, P, 1, mode, w["dtype"], S)
@@ -194,12 +222,13 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None):
             chan_ms.append(a)
             xeng_ms.append(b)
         launches = acf.launch_count() - l0
+    kept = keep(out) if keep is not None else None
     c.close()
     ops = sum(xops(N, T, C, n_sb) for T in Ts)
     return dict(ms_per_step=total_ms / steps, tops=ops / (total_ms * 1e-3) / 1e12, T=Ts,
                 chan_ms=statistics.median(chan_ms), xeng_ms=statistics.median(xeng_ms),
                 xeng_tops=xops(N, statistics.median(Ts), C, n_sb) / (statistics.median(xeng_ms) * 1e-3) / 1e12,
-                launches=launches, ops_per_step=ops / steps)
+                launches=launches, ops_per_step=ops / steps, kept=kept)
 
 
 def time_post(acf, torch, pk, N, n_sb, C, oracle_sample=True):
@@ -445,17 +474,20 @@ def main():
     # ---- headline: FP16 tensor-core mode, whole stage, inputs resident (14.4 GB > L2)
     if world > 1:
         torch.distributed.barrier()
+    # the part of each mode's last integration the oracle leg checks: subband 0,
+    # the oracle's channels, every baseline
+    keep_a12 = lambda out: torch.view_as_complex(out[0, ACC_CHANS].contiguous()).cpu().numpy().astype("complex128")
     clk = Clocks(local)
-    main_r = time_mode(acf, torch, x, w, "fp16", args.steps, args.warmup, stream)
+    main_r = time_mode(acf, torch, x, w, "fp16", args.steps, args.warmup, stream, keep=keep_a12)
     clocks = clk.stop()
     ms, value = aggregate(main_r["ms_per_step"], main_r["ops_per_step"], dev)
 
     extra = {}
     if not args.quick:
-        r3 = time_mode(acf, torch, x, w, "fp16x3", max(2, args.steps // 2), 2, stream)
+        r3 = time_mode(acf, torch, x, w, "fp16x3", max(2, args.steps // 2), 2, stream, keep=keep_a12)
         extra["fp16x3"] = dict(tops=r3["tops"], xeng_tops=r3["xeng_tops"], ms_per_step=r3["ms_per_step"],
                                issued_tensor_tops=3 * r3["xeng_tops"])
-        r32 = time_mode(acf, torch, x, w, "fp32", 2, 1, stream)
+        r32 = time_mode(acf, torch, x, w, "fp32", 2, 1, stream, keep=keep_a12)
         fp32_peak = fp32_fma_peak_tflops(torch, pk["sm_max_mhz"])
         extra["fp32_cuda_core"] = dict(tops=r32["tops"], xeng_tops=r32["xeng_tops"], ms_per_step=r32["ms_per_step"],
                                        fp32_fma_peak_tflops=fp32_peak, frac_of_fp32_peak=r32["xeng_tops"] / fp32_peak)
@@ -468,7 +500,10 @@ def main():
         torch.cuda.empty_cache()
         x6 = synth.voltages(w6["n_inputs"], w6["n_samples"], w6["n_subbands"], "ci8", w6["sigma"], None, w6["seed"],
                             device=dev)
-        r8 = time_mode(acf, torch, x6, w6, "int8", max(2, args.steps // 2), 2, stream)
+        nb64 = INT8_ACC_INPUTS * (INT8_ACC_INPUTS + 1) // 2     # baselines among the first 64 inputs
+        r8 = time_mode(acf, torch, x6, w6, "int8", max(2, args.steps // 2), 2, stream,
+                       keep=lambda out: out[0, 0, :nb64].cpu().numpy())
+        x6_sub = x6[0][:, :INT8_ACC_INPUTS].cpu().numpy()
         extra["int8_raw_a6"] = dict(tops=r8["tops"], xeng_tops=r8["xeng_tops"], ms_per_step=r8["ms_per_step"],
                                     frac_of_fp16_sustained=r8["xeng_tops"] / pk["bf16_sus"],
                                     note="exact INT8 runs on the fp16 tensor path (kind::i8 does not assemble "
@@ -518,11 +553,25 @@ def main():
         gain_r = time_gain(acf, torch, pk)
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.quick:
+        # the oracle leg: timed on subband 0 of this input (two channels, all
+        # inputs); its visibilities are also the reference for each mode's
+        # accuracy, and the exact integer oracle sums 64 inputs of the INT8 run
+        import numpy as np
+
         import oracle
         oracle.build()
-        cpu = cpu_oracle_sample()
+        cpu, Vref = cpu_oracle_sample(x[0].cpu().numpy())
         cpu.pop("seconds", None)
+        accuracy = dict(
+            metric="max |dV_ij| / sqrt(V_ii V_jj) against the fp64 oracle, subband 0, channels %s, all %d inputs "
+                   "(every baseline); INT8: bit-exact int64 on the first %d inputs of A-6 subband 0"
+                   % (ACC_CHANS, N, INT8_ACC_INPUTS),
+            tolerance=dict(fp16=3e-3, fp16x3=1e-5, fp32=1e-5),
+            fp16=norm_err(main_r["kept"], Vref, N), fp16x3=norm_err(r3["kept"], Vref, N),
+            fp32=norm_err(r32["kept"], Vref, N),
+            int8_exact=bool(np.array_equal(r8["kept"], oracle.correlate_int(x6_sub))))
 
     xeng_ms = main_r["xeng_ms"]
     achieved = main_r["xeng_tops"]
@@ -543,7 +592,8 @@ def main():
                 roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
                 channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
                                  bytes=in_bytes + out_bytes),
-                e2e=e2e, cpu_baseline=cpu, modes=extra, post=post_r, ragged_batch=batch_r, gain=gain_r)
+                e2e=e2e, cpu_baseline=cpu, accuracy=accuracy, modes=extra, post=post_r, ragged_batch=batch_r,
+                gain=gain_r)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -198,3 +198,32 @@ def test_ragged_batch_32_jobs_sampled():
             got = _gather(Vk, 0, chans, idx)
             assert _norm_err(got, ref, len(idx)) <= 1e-5
     b.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("fp16", 3e-3), ("fp16x3", 1e-5)])
+def test_a12_full_size_four_one_second_integrations(a12_input, mode, tol):
+    """The A-12 configuration's "1 s integrations x 4": one context with
+    n_integrate = 4 takes four consecutive one-second pushes (the stream is
+    the benchmark's block four times over, 781,252 samples per subband), so
+    the accumulator carries across pushes and the filter history crosses
+    three push boundaries; only the fourth push completes the integration.
+    Checked on sampled inputs and channels against the oracle's stream
+    partition."""
+    w, x = a12_input
+    N, C, P, S = w["n_inputs"], w["n_channels"], w["n_taps"], w["n_samples"]
+    chans = [0, 33]
+    with acf.Correlator(N, w["n_subbands"], C, P, 4, mode, w["dtype"], S) as c:
+        for k in range(4):
+            c.push(x)
+            V = c.visibilities()
+            assert (V is None) == (k < 3)
+        V = torch.view_as_real(V)
+        torch.cuda.synchronize()
+        for sb in (7,):
+            idx = _subset(N, 12, 500 + sb)
+            xs = x[sb][:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+            stream = np.concatenate([xs] * 4, axis=0)
+            ref = oracle.correlator(stream, P, C, push_sizes=[S] * 4, n_integrate=4, chans=chans)
+            assert len(ref) == 1
+            got = _gather(torch.view_as_complex(V), sb, chans, idx)
+            assert _norm_err(got, ref[0], len(idx)) <= tol
