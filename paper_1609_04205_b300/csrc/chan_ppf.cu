@@ -13,6 +13,7 @@
 //   4. applies w_c, converts (fp32 / fp16 / fp16 hi+lo) and stores each
 //      output row (channel, input, re|im) as MS consecutive spectra.
 #include <algorithm>
+#include <cstring>
 
 #include "acf_internal.h"
 
@@ -297,6 +298,66 @@ k_transpose_raw(const IN *__restrict__ in, long S, int N, int out_kind, void *__
     }
 }
 
+// Raw complex int8 subband -> fp16 operand rows (the INT8-exact path: int8
+// values, and scaled by a power of two, are exact in fp16).  A block moves 64
+// samples x 64 inputs: 16-byte loads of 8 inputs per time row (a row of the
+// tile is one 128-byte line), converted to half2 (re, im) into a shared tile
+// [input][time] whose 65-word rows keep the transposed reads conflict-free,
+// then 16-byte stores of 8 consecutive samples of one output row (eight lanes
+// per row: full 128-byte lines).  N must be a multiple of 8 and the samples
+// 16-byte aligned.
+__global__ void __launch_bounds__(256)
+k_transpose_ci8_f16(const uint4 *__restrict__ in, long S, int N, __half *__restrict__ out, long t_stride, float scale)
+{
+    __shared__ uint32_t tile[64 * 65];
+    const int sb = blockIdx.z;
+    const long t0 = (long)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    const int tid = threadIdx.x;
+    const __half2 sc = __float2half2_rn(scale);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = tid + 256 * k, r = e >> 3, c = e & 7;
+        const long t = t0 + r;
+        const int n = n0 + 8 * c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (t < S && n < N) v = __ldg(in + (((long)sb * S + t) * N + n) / 8);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const short re = (signed char)((w[q] >> (16 * h)) & 0xffu);
+                const short im = (signed char)((w[q] >> (16 * h + 8)) & 0xffu);
+                __half2 hv = __halves2half2(__short2half_rn(re), __short2half_rn(im));
+                if (scale != 1.f) hv = __hmul2(hv, sc);
+                uint32_t u;
+                memcpy(&u, &hv, 4);
+                tile[(8 * c + 2 * q + h) * 65 + r] = u;
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, g = lane & 7;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int nl = (warp + 8 * k) * 4 + (lane >> 3);
+        const int n = n0 + nl;
+        uint32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = tile[nl * 65 + 8 * g + j];
+        const uint4 re = make_uint4(__byte_perm(v[0], v[1], 0x5410), __byte_perm(v[2], v[3], 0x5410),
+                                    __byte_perm(v[4], v[5], 0x5410), __byte_perm(v[6], v[7], 0x5410));
+        const uint4 im = make_uint4(__byte_perm(v[0], v[1], 0x7632), __byte_perm(v[2], v[3], 0x7632),
+                                    __byte_perm(v[4], v[5], 0x7632), __byte_perm(v[6], v[7], 0x7632));
+        if (n < N) {
+            const long col = t0 + 8 * g;
+            *reinterpret_cast<uint4 *>(out + ((long)sb * 2 * N + 2L * n) * t_stride + col) = re;
+            *reinterpret_cast<uint4 *>(out + ((long)sb * 2 * N + 2L * n + 1) * t_stride + col) = im;
+        }
+    }
+}
+
 template <typename E>
 __global__ void k_history(const E *__restrict__ hist, long n_hist, const E *__restrict__ in,
                           long n_samples, int N, long from, long count, E *__restrict__ dst,
@@ -430,6 +491,13 @@ cudaError_t launch_transpose_raw(const void *samples, long n_samples, acf_in_dty
 {
     const long T64 = round_up(n_samples, 64);
     if (T64 == 0) return cudaSuccess;
+    if (dt == ACF_IN_CI8 && out_kind == OUT_F16 && N % 8 == 0 && reinterpret_cast<uintptr_t>(samples) % 16 == 0) {
+        dim3 g8((unsigned)(T64 / 64), (N + 63) / 64, n_sb);
+        k_transpose_ci8_f16<<<g8, 256, 0, s>>>(static_cast<const uint4 *>(samples), n_samples, N,
+                                                static_cast<__half *>(out), t_stride, scale);
+        g_launches++;
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)(T64 / 64), (N + 31) / 32, n_sb);
     switch (dt) {
     case ACF_IN_CI8:  k_transpose_raw<char2><<<grid, 256, 0, s>>>(static_cast<const char2 *>(samples), n_samples, N, out_kind, out, out_lo, t_stride, scale); break;

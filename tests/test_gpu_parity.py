@@ -153,6 +153,22 @@ def test_correlator_64ch_streaming_pushes_ci16():
             assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
 
 
+@pytest.mark.parametrize("N,S,scale", [(8, 64, 1.0), (64, 1000, 1.0), (72, 777, 1.0), (96, 5000, 0.5),
+                                         (1152, 300, 1.0), (5, 130, 1.0)])
+def test_transpose_raw_ci8_fp16_exact(N, S, scale):
+    """Raw-subband operand (the transpose of Sec. 4.2.4 alone) from complex int8
+    to fp16 rows: every value is the exact int8 times the power-of-two scale,
+    rows 2n / 2n + 1 hold Re / Im of input n, the tail past S is zero.  N a
+    multiple of 8 takes the 16-byte tiled kernel, other counts the generic one."""
+    _dev()
+    x = _samples(N, S, 2, "ci8", sigma=40.0, n_src=0, seed=N + S)
+    Xh, _ = acf.transpose_raw(x, out_kind="f16", scale=scale)
+    torch.cuda.synchronize()
+    want = x.permute(0, 2, 3, 1).reshape(2, 2 * N, S).float() * scale       # [sb][2n + comp][t]
+    assert torch.equal(Xh[..., :S].float(), want)
+    assert (Xh[..., S:] == 0).all()
+
+
 # ---------------------------------------------------------------- X-engines
 @pytest.mark.parametrize("N,T", [(1, 1), (3, 37), (64, 100), (97, 500), (130, 64)])
 def test_xengine_simt_vs_oracle(N, T):
