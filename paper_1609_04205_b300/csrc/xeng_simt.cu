@@ -1,19 +1,31 @@
 // Plain fp32 CUDA-core X-engine (Sec. 4.2.5): the comparison path.
 //
-// The paper's design divides each channel's covariance triangle into
-// squares of 32x32 receivers, one work-group each, every thread holding a
-// 2x2 receiver tile in registers across the time loop.  Here the square is
-// 64x64 complex inputs per 256-thread block and each thread keeps a 4x4 tile
-// (four loads per complex MAC pair instead of two), staged through shared
-// memory 32 spectra at a time.  Accumulation is two-level: fp32 partial sums
-// over chunks of 4096 spectra are folded into fp32 totals, which keeps the
-// rounding error of long raw-subband integrations near sqrt(T)*2^-24 relative.
+// The paper's design divides each channel's covariance triangle into squares
+// of 32x32 receivers, one work-group each, every thread holding a 2x2
+// receiver tile in registers across the time loop.  Here a 128-thread block
+// owns a 64x64 square of complex inputs and each thread an 8x4 tile (rows
+// ty + 8a, columns tx + 16b), so every operand value a thread loads from
+// shared memory feeds 4 (row) or 8 (column) complex multiply-accumulates.
+// Each complex MAC V_ij += x_i conj(y_j) is two packed fp32x2 FMAs on
+//   (re, im) += (xr, xi) * (yr, yr)   and   (re, im) += (xi, xr) * (yi, -yi),
+// so the shared stages hold the rows pre-arranged as (xr, xi, xi, xr) and the
+// columns as (yr, yr, yi, -yi): one 16-byte load per operand per MAC pair.
+// Stages of 16 spectra are double buffered: the next stage's global loads
+// (four lanes per 64-byte row piece) are in flight while the current one is
+// multiplied.  Partial sums are flushed to
+// V with atomic adds every CHUNK spectra (V is zeroed by the caller), which
+// keeps the rounding error of long raw-subband integrations near
+// sqrt(T / CHUNK) * 2^-24 relative.
 #include "acf_internal.h"
 
 namespace acf {
 namespace {
 
-constexpr int TILE = 64, KT = 32, CHUNK = 4096;
+constexpr int BT = 64;          // complex inputs per tile side
+constexpr int KT = 16;          // spectra per stage
+constexpr int NTH = 128;        // threads per block
+constexpr int CHUNK = 4096;     // spectra per partial sum
+constexpr size_t SMEM_SIMT = 2ull * 2 * KT * BT * sizeof(float4);   // A and B, two buffers: 64 KB
 
 __device__ __forceinline__ void tri_decode(int k, int &bi, int &bj) {
     int b = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
@@ -23,100 +35,120 @@ __device__ __forceinline__ void tri_decode(int k, int &bi, int &bj) {
     bj = k - b * (b + 1) / 2;
 }
 
-__global__ void __launch_bounds__(256)
-k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, float vscale,
-            float2 *__restrict__ V)
+// Four spectra t .. t + 3 of one operand row; zeros past n_time.
+__device__ __forceinline__ float4 row4(const float *src, long t, long n_time) {
+    if (t + 3 < n_time) return __ldg(reinterpret_cast<const float4 *>(src + t));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t + 0 < n_time) v.x = __ldg(src + t);
+    if (t + 1 < n_time) v.y = __ldg(src + t + 1);
+    if (t + 2 < n_time) v.z = __ldg(src + t + 2);
+    return v;
+}
+
+__global__ void __launch_bounds__(NTH, 3)
+k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, float vscale, float2 *__restrict__ V)
 {
-    __shared__ float As[KT][2][TILE + 4];
-    __shared__ float Bs[KT][2][TILE + 4];
+    extern __shared__ __align__(16) float4 sm[];
+    float4 (*As)[KT][BT] = reinterpret_cast<float4 (*)[KT][BT]>(sm);                 // [buf][t][i]
+    float4 (*Bs)[KT][BT] = reinterpret_cast<float4 (*)[KT][BT]>(sm + 2 * KT * BT);  // [buf][t][j]
     int bi, bj;
     tri_decode(blockIdx.x, bi, bj);
     const long p = blockIdx.y;
     const float *xp = x + p * 2L * N * t_stride;
-    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-    const int i0 = bi * TILE, j0 = bj * TILE;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int i0 = bi * BT, j0 = bj * BT;
 
-    float ar[4][4], ai[4][4], tr[4][4], ti[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = tr[a][b] = ti[a][b] = 0.f;
+    // staging: threads 0-63 stage the A rows, 64-127 the B rows.  A thread
+    // covers (4-spectrum group tg, input il) for il = il0 + 16 q: four lanes
+    // read one row's 16 spectra (64 contiguous bytes), a warp 8 rows.  The
+    // stage column of (t, i) is i ^ sw(t), sw(t) = 2 * ((t >> 2) & 3), which
+    // keeps the transposing 16-byte stores of a quarter-warp (4 groups x 2
+    // inputs) on distinct banks; the MAC loads apply the same swizzle.
+    const int se = tid & 63, tg = se & 3, il0 = se >> 2;
+    const bool stage_b = tid >= 64;
+    const int nbase = stage_b ? j0 : i0;
+    float4 pre[4][2];            // (q, re | im): 4 spectra each
 
+    auto fetch = [&](long t0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = nbase + il0 + 16 * q;
+            if (n < N) {
+                const float *re_row = xp + 2L * n * t_stride;
+                pre[q][0] = row4(re_row, t0 + 4 * tg, n_time);
+                pre[q][1] = row4(re_row + t_stride, t0 + 4 * tg, n_time);
+            } else {
+                pre[q][0] = pre[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    auto deposit = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = (il0 + 16 * q) ^ (2 * tg);
+            const float r[4] = {pre[q][0].x, pre[q][0].y, pre[q][0].z, pre[q][0].w};
+            const float m[4] = {pre[q][1].x, pre[q][1].y, pre[q][1].z, pre[q][1].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (stage_b) Bs[buf][4 * tg + k][col] = make_float4(r[k], r[k], m[k], -m[k]);
+                else As[buf][4 * tg + k][col] = make_float4(r[k], m[k], m[k], r[k]);
+            }
+        }
+    };
+
+    float2 acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+
+    const long NB = (long)N * (N + 1) / 2;
+    auto flush = [&]() {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = i0 + ty + 8 * a, j = j0 + tx + 16 * b;
+                if (i < N && j <= i)
+                    atomicAdd(&V[p * NB + (long)i * (i + 1) / 2 + j], make_float2(acc[a][b].x * vscale, acc[a][b].y * vscale));
+                acc[a][b] = make_float2(0.f, 0.f);
+            }
+    };
+
+    fetch(0);
+    deposit(0);
+    __syncthreads();
+    int buf = 0;
     long since = 0;
     for (long t0 = 0; t0 < n_time; t0 += KT) {
-        // stage 64 inputs x (re, im) x 32 spectra for both row blocks
-        for (int e = tid; e < 2 * TILE * 2 * (KT / 4); e += 256) {
-            const int which = e / (TILE * 2 * (KT / 4));        // 0 = A rows, 1 = B rows
-            const int r = (e / (KT / 4)) % (TILE * 2);          // local real row
-            const int seg = e % (KT / 4);
-            const int n = (which ? j0 : i0) + (r >> 1);
-            const int comp = r & 1;
-            const long t = t0 + seg * 4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (n < N) {
-                const float *src = xp + (2L * n + comp) * t_stride + t;
-                if (t + 3 < n_time) {
-                    v = *reinterpret_cast<const float4 *>(src);
-                } else {
-                    if (t + 0 < n_time) v.x = src[0];
-                    if (t + 1 < n_time) v.y = src[1];
-                    if (t + 2 < n_time) v.z = src[2];
-                }
-            }
-            float (*S)[2][TILE + 4] = which ? Bs : As;
-            S[seg * 4 + 0][comp][r >> 1] = v.x;
-            S[seg * 4 + 1][comp][r >> 1] = v.y;
-            S[seg * 4 + 2][comp][r >> 1] = v.z;
-            S[seg * 4 + 3][comp][r >> 1] = v.w;
-        }
-        __syncthreads();
+        const bool more = t0 + KT < n_time;
+        if (more) fetch(t0 + KT);            // in flight during this stage's MACs
 #pragma unroll 4
         for (int tt = 0; tt < KT; ++tt) {
-            float xr[4], xi[4], yr[4], yi[4];
+            const int sw = 2 * ((tt >> 2) & 3);
+            float4 av[8], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                xr[a] = As[tt][0][ty + 16 * a];
-                xi[a] = As[tt][1][ty + 16 * a];
-                yr[a] = Bs[tt][0][tx + 16 * a];
-                yi[a] = Bs[tt][1][tx + 16 * a];
-            }
+            for (int a = 0; a < 8; ++a) av[a] = As[buf][tt][(ty + 8 * a) ^ sw];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][tt][(tx + 16 * b) ^ sw];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    // x_i conj(y_j)
-                    ar[a][b] = fmaf(xr[a], yr[b], ar[a][b]);
-                    ar[a][b] = fmaf(xi[a], yi[b], ar[a][b]);
-                    ai[a][b] = fmaf(xi[a], yr[b], ai[a][b]);
-                    ai[a][b] = fmaf(-xr[a], yi[b], ai[a][b]);
+                    acc[a][b] = __ffma2_rn(make_float2(av[a].x, av[a].y), make_float2(bv[b].x, bv[b].y), acc[a][b]);
+                    acc[a][b] = __ffma2_rn(make_float2(av[a].z, av[a].w), make_float2(bv[b].z, bv[b].w), acc[a][b]);
                 }
         }
-        __syncthreads();
         since += KT;
-        if (since >= CHUNK) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    tr[a][b] += ar[a][b];
-                    ti[a][b] += ai[a][b];
-                    ar[a][b] = ai[a][b] = 0.f;
-                }
+        if (since >= CHUNK && more) {
+            flush();
             since = 0;
         }
+        if (more) deposit(buf ^ 1);          // the other buffer: last read before the previous barrier
+        __syncthreads();
+        buf ^= 1;
     }
-    const long NB = (long)N * (N + 1) / 2;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
-            if (i < N && j <= i) {
-                const float re = (tr[a][b] + ar[a][b]) * vscale;
-                const float im = (ti[a][b] + ai[a][b]) * vscale;
-                atomicAdd(&V[p * NB + (long)i * (i + 1) / 2 + j], make_float2(re, im));
-            }
-        }
+    flush();
 }
 
 }  // namespace
@@ -125,9 +157,12 @@ cudaError_t launch_xeng_simt(const float *x, int n_problems, int N, long n_time,
                              float vscale, float2 *V, cudaStream_t s)
 {
     if (n_problems <= 0 || N <= 0 || n_time <= 0) return cudaSuccess;
-    const int nt = (N + TILE - 1) / TILE;
+    if (n_problems > 65535) return cudaErrorInvalidValue;
+    const int nt = (N + BT - 1) / BT;
+    cudaError_t e = cudaFuncSetAttribute(k_xeng_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_SIMT);
+    if (e != cudaSuccess) return e;
     dim3 grid(nt * (nt + 1) / 2, n_problems);
-    k_xeng_simt<<<grid, 256, 0, s>>>(x, N, n_time, t_stride, vscale, V);
+    k_xeng_simt<<<grid, NTH, SMEM_SIMT, s>>>(x, N, n_time, t_stride, vscale, V);
     g_launches++;
     return cudaGetLastError();
 }
