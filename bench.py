@@ -414,7 +414,8 @@ def profile_case(mode):
 
 def post_case():
     """The post-correlation kernels alone on the A-12 visibility set (the same
-    calls as the bench line's `post` object, without the oracle), for profiling."""
+    calls as the bench line's `post` object, without the oracle), then the gain
+    forward/adjoint, for profiling."""
     import torch
 
     import paper_1609_04205_b300 as acf
@@ -422,6 +423,8 @@ def post_case():
     for k, v in r.items():
         if isinstance(v, dict):
             print("%-26s %8.3f ms %8.1f GB/s  frac %.3f" % (k, v["ms"], v["gbs"], v["frac_hbm"]))
+    v = time_gain(acf, torch, peaks())
+    print("%-26s %8.3f ms %8.1f GB/s  frac %.3f" % ("gain_forward", v["ms"], v["gbs"], v["frac_hbm"]))
     return 0
 
 

@@ -89,6 +89,7 @@ struct TcJob {
     int mode;             // ACF_X_FP16, ACF_X_FP16x3 or ACF_X_INT8
     float vscale;
     int store = 0;        // 1: overwrite V (allowed only when one work item owns each tile)
+    const float2 *rot = nullptr;   // delay compensation a[problem][input] applied in the flush, or nullptr
 };
 struct TcPlan;            // opaque: tensor maps + work list on the device
 struct TcTuning {
@@ -103,6 +104,10 @@ cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s);
 // Per-launch job parameters: valid spectra, the fp result scale, and whether
 // the launch may overwrite V (granted only when the job has no time split).
 cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale, int store);
+// Delay compensation for a job's float results from now on (nullptr: off):
+// every visibility the flush writes becomes V_ij a_i conj(a_j), a[p][i] from
+// launch_delay_table.
+cudaError_t tc_plan_set_rot(TcPlan *p, int job, const float2 *rot);
 int tc_plan_job_stores(const TcPlan *p, int job);   // 1 when the job overwrites V
 int tc_plan_job_split(const TcPlan *p, int job);
 int tc_plan_items(const TcPlan *p);

@@ -9,8 +9,9 @@
 // conjugate) to a per-block partial, and accumulates the gradient rows
 //   grad_i += 4 E_ij conj(R_ij) g_j      and, for i != j,
 //   grad_j += 4 conj(E_ij) R_ij g_i      (= 4 E_ji conj(R_ji) g_i).
-// Row sums are warp-reduced, column sums go through shared-memory atomics,
-// and one global atomic per (tile row/column) lands in grad.  The per-block
+// Row sums are warp-reduced; each lane keeps the column sums of its two tile
+// columns in registers, the warps' sums are combined once per tile in shared
+// memory, and one global atomic per (tile row/column) lands in grad.  The per-block
 // loss partials are summed by a second, single-block kernel in a fixed order,
 // so the loss is deterministic.
 #include <mutex>
@@ -39,8 +40,8 @@ __global__ void __launch_bounds__(256)
 k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 *__restrict__ g,
        int N, float *__restrict__ partials, float2 *__restrict__ grad)
 {
-    __shared__ float2 colacc[GT];
     __shared__ float2 gi_s[GT], gj_s[GT];
+    __shared__ float2 colred[8][GT];
     __shared__ float red[8];
     int bi, bj;
     tri_decode_g(blockIdx.x, bi, bj);
@@ -51,39 +52,52 @@ k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 
     const float2 *Vc = V + (long)c * NB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < GT) {
-        colacc[tid] = make_float2(0.f, 0.f);
         gi_s[tid] = (i0 + tid < N) ? g[i0 + tid] : make_float2(0.f, 0.f);
         gj_s[tid] = (j0 + tid < N) ? g[j0 + tid] : make_float2(0.f, 0.f);
     }
     __syncthreads();
+    // lane owns tile columns jj = lane and lane + 32: its g_j, and the column
+    // sums of the rows its warp walks, stay in registers
+    const float2 gj[2] = {gj_s[lane], gj_s[lane + 32]};
+    float2 col[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     float loss = 0.f;
-    // each warp walks rows; lane covers columns jj = lane and lane + 32
-    for (int ii = warp; ii < GT; ii += 8) {
-        const int i = i0 + ii;
-        float2 rowsum = make_float2(0.f, 0.f);
-        if (i < N) {
-            const long base = (long)i * (i + 1) / 2;
+    // the warp's 8 rows (ii = warp + 8k): all 32 loads first, then the
+    // arithmetic; elements outside the triangle load as zero, so E = 0 there
+    // and they add nothing
+    float2 rr[8][2], vv[8][2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int jj = lane + 32 * h;
-                const int j = j0 + jj;
-                if (j <= i && j < N) {
-                    const float2 r = Rc[base + j], v = Vc[base + j];
-                    const float2 gi = gi_s[ii], gj = gj_s[jj];
-                    const float2 m = cmulf(cmulf(gi, r), conjf2(gj));
-                    const float2 e = make_float2(m.x - v.x, m.y - v.y);
-                    const float w = (i == j) ? 1.f : 2.f;
-                    loss = fmaf(w, e.x * e.x + e.y * e.y, loss);
-                    if (grad) {
-                        const float2 t = cmulf(cmulf(e, conjf2(r)), gj);
-                        rowsum.x += t.x;
-                        rowsum.y += t.y;
-                        if (i != j) {
-                            const float2 u = cmulf(cmulf(conjf2(e), r), gi);
-                            atomicAdd(&colacc[jj].x, u.x);
-                            atomicAdd(&colacc[jj].y, u.y);
-                        }
-                    }
+    for (int k = 0; k < 8; ++k) {
+        const int i = i0 + warp + 8 * k;
+        const long base = (long)i * (i + 1) / 2;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + lane + 32 * h;
+            const bool in = i < N && j <= i;
+            rr[k][h] = in ? __ldg(Rc + base + j) : make_float2(0.f, 0.f);
+            vv[k][h] = in ? __ldg(Vc + base + j) : make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int ii = warp + 8 * k, i = i0 + ii;
+        const float2 gi = gi_s[ii];
+        float2 rowsum = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + lane + 32 * h;
+            const float2 r = rr[k][h], v = vv[k][h];
+            const float2 m = cmulf(cmulf(gi, r), conjf2(gj[h]));
+            const float2 e = make_float2(m.x - v.x, m.y - v.y);
+            const float w = (i == j) ? 1.f : 2.f;
+            loss = fmaf(w, e.x * e.x + e.y * e.y, loss);
+            if (grad) {
+                const float2 t = cmulf(cmulf(e, conjf2(r)), gj[h]);
+                rowsum.x += t.x;
+                rowsum.y += t.y;
+                if (i != j) {
+                    const float2 u = cmulf(cmulf(conjf2(e), r), gi);
+                    col[h].x += u.x;
+                    col[h].y += u.y;
                 }
             }
         }
@@ -99,6 +113,10 @@ k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
     if (lane == 0) red[warp] = loss;
+    if (grad) {
+        colred[warp][lane] = col[0];
+        colred[warp][lane + 32] = col[1];
+    }
     __syncthreads();
     if (tid == 0) {
         float s = 0.f;
@@ -106,7 +124,12 @@ k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 
         partials[(long)blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
     if (grad && tid < GT && j0 + tid < N) {
-        const float2 v = colacc[tid];
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            v.x += colred[w][tid].x;
+            v.y += colred[w][tid].y;
+        }
         if (v.x != 0.f || v.y != 0.f) atomicAdd(&grad[j0 + tid], make_float2(4.f * v.x, 4.f * v.y));
     }
 }

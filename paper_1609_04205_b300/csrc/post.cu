@@ -39,16 +39,16 @@ __device__ __forceinline__ void df_add_sq(float a, float &sh, float &sl)
 }
 __device__ __forceinline__ double df_value(float sh, float sl) { return (double)sh + (double)sl; }
 
-// Exact-in-effect test of |v|^2 > t (t fp64, tf = (float)t): an fp32 square
-// (error < 2^-23) decides outside a 2^-20 guard band around tf; inside it the
-// fp64 square decides.
-__device__ __forceinline__ bool pow_above(float2 v, double t, float tf)
-{
-    const float pf = fmaf(v.x, v.x, v.y * v.y);
-    if (pf > tf * (1.f + 0x1p-20f)) return true;
-    if (pf < tf * (1.f - 0x1p-20f)) return false;
-    return (double)v.x * v.x + (double)v.y * v.y > t;
-}
+// Exact-in-effect tests of |v|^2 > t: the fp32 square pf = fma(x, x, y*y)
+// (relative error below 2^-23) is compared with a threshold tf that carries a
+// relative error of at most 2^-22, widened by a 2^-20 guard band on either
+// side; outside the band the fp32 verdict equals the exact one, inside it the
+// caller settles the element with the fp64 square (exact for fp32 inputs up
+// to the final rounding) against the fp64 threshold.  The fp64 work stays out
+// of the per-element loops (band hits are collected in bit masks and settled
+// afterwards), so the loops run at fp32 rate.
+constexpr float kBandLo = 1.f - 0x1p-20f, kBandHi = 1.f + 0x1p-20f;
+__device__ __forceinline__ double pow2_f64(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
 
 // a[p][i] = exp(+2 pi i f_p d_i), f_p the sky frequency of problem p's channel
 // (natural DFT order: channel c at f_centre + c' fs / C, c' = c for 2c < C,
@@ -146,19 +146,37 @@ __global__ void k_integrate_scalar(const T *__restrict__ in, T *__restrict__ out
 }
 
 // Per problem: sum of |V|^2 over all baselines and over the autocorrelations,
-// in fp64 (sum[p][0] all, sum[p][1] autos).
+// in fp64 (sum[p][0] all, sum[p][1] autos).  With NB even every problem row
+// starts on a 16-byte boundary and a thread reads two baselines per float4,
+// four loads in flight.
+template <bool VEC>
 __global__ void k_clip_sums(const float2 *__restrict__ V, long NB, int N, double *__restrict__ sums)
 {
     const long p = blockIdx.y;
     const float2 *row = V + p * NB;
     float sh = 0.f, sl = 0.f;
-    for (long b = blockIdx.x * (long)blockDim.x + threadIdx.x; b < NB; b += (long)gridDim.x * blockDim.x) {
-        const float2 v = row[b];
-        df_add_sq(v.x, sh, sl);
-        df_add_sq(v.y, sh, sl);
+    const long stride = (long)gridDim.x * blockDim.x;
+    const long first = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (VEC) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+        const long n4 = NB / 2;
+#pragma unroll 4
+        for (long b = first; b < n4; b += stride) {
+            const float4 v = __ldcs(r4 + b);
+            df_add_sq(v.x, sh, sl);
+            df_add_sq(v.y, sh, sl);
+            df_add_sq(v.z, sh, sl);
+            df_add_sq(v.w, sh, sl);
+        }
+    } else {
+        for (long b = first; b < NB; b += stride) {
+            const float2 v = row[b];
+            df_add_sq(v.x, sh, sl);
+            df_add_sq(v.y, sh, sl);
+        }
     }
     double all = df_value(sh, sl), aut = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    for (long i = first; i < N; i += stride) {
         const float2 v = row[i * (i + 1) / 2 + i];
         aut += (double)v.x * v.x + (double)v.y * v.y;
     }
@@ -199,51 +217,141 @@ __global__ void k_clip_thr(const double *__restrict__ sums, long n_prob, long n_
     thr_f[p] = (float)(k1sq * ms);
 }
 
-// Flags for one (subband, baseline) across its C channels (C <= 256).  Stage 1
-// (per channel): |V|^2 > thr[channel] = k1^2 * mean over the channel's
-// cross-correlations.  Stage 2 (per baseline): |V|^2 > k2^2 * mean of |V|^2
-// over the channels stage 1 kept.  Both tests go through pow_above (fp32
-// with a guard band, fp64 inside it), so every decision equals the fp64
-// comparison of the exact squares; the stage-2 sum is a double-float sum of
-// exact squares.  Stage-1 results stay in register bit masks; each flag byte
-// is written once.  Autocorrelations are never flagged.
-__global__ void k_clip_flags(const float2 *__restrict__ V, long NB, int N, int C, const double *__restrict__ thr,
-                             const float *__restrict__ thr_f, double k2sq, unsigned char *__restrict__ flags)
+// Flags for one (subband, baseline) across its C <= CMAX channels, one thread
+// per baseline, 128 baselines per block.  Stage 1 (per channel): |V|^2 >
+// thr[channel] = k1^2 * mean over the channel's cross-correlations.  Stage 2
+// (per baseline): |V|^2 > k2^2 * mean of |V|^2 over the channels stage 1
+// kept, the mean a double-float sum of exact squares.  Both tests are exact in
+// effect (fp32 outside a guard band, fp64 inside it), so every decision
+// equals the fp64 comparison of the exact squares.  The stage-2 fp32
+// threshold k2^2 * ((sh + sl) / n) takes four fp32 roundings (at most 2^-22
+// relative); its fp64 form is formed only when some element lands in the band.
+// Loads go out in branch-free batches of 8 channels; stage 2 re-reads the
+// baseline's values, which are still in L2.  The flag bytes are collected in
+// shared memory and written per channel as one 128-byte run with 16-byte
+// stores (single-byte stores from scattered warps leave partial lines that
+// cost DRAM read-modify-writes).  Autocorrelations are never flagged.
+template <int CMAX>
+__global__ void __launch_bounds__(128)
+k_clip_flags(const float2 *__restrict__ V, long NB, int N, int C, const double *__restrict__ thr,
+             const float *__restrict__ thr_f, double k2sq, unsigned char *__restrict__ flags)
 {
-    const long b = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (b >= NB) return;
-    const int s = blockIdx.y;
-    const int i = tri_row(b);
-    const bool cross = (long)i * (i + 1) / 2 + i != b;
-    const float2 *col = V + (long)s * C * NB + b;
-    unsigned char *fl = flags + (long)s * C * NB + b;
-    if (!cross) {
-        for (int c = 0; c < C; ++c) fl[(long)c * NB] = 0;
-        return;
+    constexpr int NW = CMAX / 64, D = 8;
+    __shared__ double th[CMAX];
+    __shared__ float lo1[CMAX], hi1[CMAX];
+    __shared__ __align__(16) unsigned char sf[CMAX][128];
+    const int s = blockIdx.y, tid = threadIdx.x;
+    for (int c = tid; c < C; c += blockDim.x) {
+        th[c] = thr[(long)s * C + c];
+        const float tf = thr_f[(long)s * C + c];
+        lo1[c] = tf * kBandLo;
+        hi1[c] = tf * kBandHi;
     }
-    const double *th = thr + (long)s * C;
-    const float *thf = thr_f + (long)s * C;
-    uint32_t f1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float sh = 0.f, sl = 0.f;
-    int n_keep = 0;
-#pragma unroll 8
-    for (int c = 0; c < C; ++c) {
-        const float2 v = col[(long)c * NB];
-        if (pow_above(v, th[c], thf[c])) {
-            f1[c >> 5] |= 1u << (c & 31);
+    __syncthreads();
+    const long b0 = (long)blockIdx.x * 128, b = b0 + tid;
+    if (b < NB) {
+        const int i = tri_row(b);
+        if ((long)i * (i + 1) / 2 + i == b) {
+            for (int c = 0; c < C; ++c) sf[c][tid] = 0;
         } else {
-            df_add_sq(v.x, sh, sl);
-            df_add_sq(v.y, sh, sl);
-            ++n_keep;
+            const float2 *col = V + (long)s * C * NB + b;
+            uint64_t f1[NW];
+            float sh = 0.f, sl = 0.f;
+            int n_keep = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                f1[w] = 0;
+                uint64_t amb = 0;
+                const int cb = 64 * w, ce = min(C, cb + 64);
+                for (int c0 = cb; c0 < ce; c0 += D) {
+                    float2 v[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        v[k] = c0 + k < ce ? __ldcg(col + (long)(c0 + k) * NB) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const int c = c0 + k;
+                        if (c < ce) {
+                            const float pf = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+                            const uint64_t bit = 1ull << (c - cb);
+                            if (pf > hi1[c]) {
+                                f1[w] |= bit;
+                            } else if (pf < lo1[c]) {
+                                df_add_sq(v[k].x, sh, sl);
+                                df_add_sq(v[k].y, sh, sl);
+                                ++n_keep;
+                            } else {
+                                amb |= bit;
+                            }
+                        }
+                    }
+                }
+                while (amb) {                       // guard-band channels, in fp64
+                    const int k = __ffsll((long long)amb) - 1;
+                    amb &= amb - 1;
+                    const float2 v = col[(long)(cb + k) * NB];
+                    if (pow2_f64(v) > th[cb + k]) {
+                        f1[w] |= 1ull << k;
+                    } else {
+                        df_add_sq(v.x, sh, sl);
+                        df_add_sq(v.y, sh, sl);
+                        ++n_keep;
+                    }
+                }
+            }
+            const float t2f = n_keep > 0 ? (float)k2sq * ((sh + sl) / (float)n_keep) : 0.f;
+            const float lo2 = t2f * kBandLo, hi2 = t2f * kBandHi;
+            uint64_t amb2[NW];
+            bool any = false;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                amb2[w] = 0;
+                const int cb = 64 * w, ce = min(C, cb + 64);
+                for (int c0 = cb; c0 < ce; c0 += D) {
+                    float2 v[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        v[k] = c0 + k < ce ? __ldcs(col + (long)(c0 + k) * NB) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const int c = c0 + k;
+                        if (c < ce) {
+                            unsigned char f = (f1[w] >> (c - cb)) & 1u;
+                            if (!f) {
+                                const float pf = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+                                if (pf > hi2) f = 1;
+                                else if (pf >= lo2) amb2[w] |= 1ull << (c - cb);
+                            }
+                            sf[c][tid] = f;
+                        }
+                    }
+                }
+                any |= amb2[w] != 0;
+            }
+            if (any) {
+                const double t2 = n_keep > 0 ? k2sq * (df_value(sh, sl) / n_keep) : 0.0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    while (amb2[w]) {
+                        const int k = __ffsll((long long)amb2[w]) - 1;
+                        amb2[w] &= amb2[w] - 1;
+                        sf[64 * w + k][tid] = pow2_f64(col[(long)(64 * w + k) * NB]) > t2 ? 1 : 0;
+                    }
+                }
+            }
         }
     }
-    const double t2 = n_keep > 0 ? k2sq * (df_value(sh, sl) / n_keep) : 0.0;
-    const float t2f = (float)t2;
-#pragma unroll 8
-    for (int c = 0; c < C; ++c) {
-        unsigned char f = (f1[c >> 5] >> (c & 31)) & 1u;
-        if (!f) f = pow_above(col[(long)c * NB], t2, t2f) ? 1 : 0;
-        fl[(long)c * NB] = f;
+    __syncthreads();
+    const long nval = NB - b0 < 128 ? NB - b0 : 128;
+    unsigned char *fs = flags + (long)s * C * NB + b0;
+    for (int idx = tid; idx < C * 8; idx += blockDim.x) {
+        const int c = idx >> 3, q = idx & 7;
+        unsigned char *dst = fs + (long)c * NB;
+        if (nval == 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            __stcs(reinterpret_cast<uint4 *>(dst) + q, reinterpret_cast<const uint4 *>(sf[c])[q]);
+        } else {
+            for (int k = 16 * q; k < 16 * q + 16 && k < nval; ++k) dst[k] = sf[c][k];
+        }
     }
 }
 
@@ -367,16 +475,23 @@ cudaError_t launch_sigma_clip(const float2 *V, int n_sb, int C, int N, double k1
     const long n_prob = (long)n_sb * C;
     cudaError_t e = cudaMemsetAsync(d_sums, 0, sizeof(double) * 2 * n_prob, s);
     if (e != cudaSuccess) return e;
+    const bool vec = NB % 2 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0;
     const unsigned bx = (unsigned)std::min<long>((NB + 255) / 256, 64);
-    k_clip_sums<<<dim3(bx, (unsigned)n_prob), 256, 0, s>>>(V, NB, N, d_sums);
+    if (vec)
+        k_clip_sums<true><<<dim3(bx, (unsigned)n_prob), 256, 0, s>>>(V, NB, N, d_sums);
+    else
+        k_clip_sums<false><<<dim3(bx, (unsigned)n_prob), 256, 0, s>>>(V, NB, N, d_sums);
     g_launches++;
     double *thr = d_sums + 2 * n_prob;
     float *thr_f = reinterpret_cast<float *>(thr + n_prob);
     k_clip_thr<<<(unsigned)((n_prob + 255) / 256), 256, 0, s>>>(d_sums, n_prob, (long)N * (N - 1) / 2, k1 * k1, thr,
                                                                thr_f);
     g_launches++;
-    k_clip_flags<<<dim3((unsigned)((NB + 127) / 128), (unsigned)n_sb), 128, 0, s>>>(V, NB, N, C, thr, thr_f, k2 * k2,
-                                                                                flags);
+    const dim3 fgrid((unsigned)((NB + 127) / 128), (unsigned)n_sb);
+    if (C <= 64)
+        k_clip_flags<64><<<fgrid, 128, 0, s>>>(V, NB, N, C, thr, thr_f, k2 * k2, flags);
+    else
+        k_clip_flags<256><<<fgrid, 128, 0, s>>>(V, NB, N, C, thr, thr_f, k2 * k2, flags);
     g_launches++;
     return cudaGetLastError();
 }

@@ -149,6 +149,7 @@ static cudaError_t make_plan(acf_ctx *c, std::string *perr)
     j.t_stride = c->t_stride;
     j.mode = c->mode;
     j.vscale = 1.f / (c->scale * c->scale);
+    j.rot = c->d_delay_tab;
     TcTuning tun;
     tun.pair = c->variant;
     return tc_plan_create(&j, 1, tun, &c->plan, perr);
@@ -489,8 +490,10 @@ acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_
     *n_ready = 0;
     if (!c->ready) return ACF_OK;
     cudaError_t e = cudaSuccess;
-    if (c->d_delay_tab) {
-        // the accumulator is reset when the next integration starts, so rotate it in place
+    if (c->d_delay_tab && c->mode == ACF_X_FP32) {
+        // the fp32 CUDA-core path has no fused rotation: the accumulator is
+        // reset when the next integration starts, so rotate it in place (the
+        // tensor-core X-engine applies the table in its flush)
         e = launch_delay_apply(static_cast<float2 *>(c->d_V), c->d_delay_tab, (long)c->n_sb * c->C, c->N,
                                (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "delay compensation");
@@ -509,6 +512,7 @@ acf_status acf_set_delays(acf_ctx *c, const double *delays, const double *f_cent
     if (c->pushes != 0) return fail(c, ACF_ESTATE, "delays can only change between integrations");
     if (!delays) {
         cudaError_t e = cudaDeviceSynchronize();
+        if (c->plan) tc_plan_set_rot(c->plan, 0, nullptr);
         cudaFree(c->d_delay_tab);
         c->d_delay_tab = nullptr;
         return e == cudaSuccess ? ACF_OK : cuda_fail(c, e, "sync");
@@ -538,6 +542,7 @@ acf_status acf_set_delays(acf_ctx *c, const double *delays, const double *f_cent
     if (e == cudaSuccess) e = launch_delay_table(tmp, tmp + c->N, sample_rate, c->n_sb, c->C, c->N, c->d_delay_tab, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(tmp);
+    if (e == cudaSuccess && c->plan) e = tc_plan_set_rot(c->plan, 0, c->d_delay_tab);
     return e == cudaSuccess ? ACF_OK : cuda_fail(c, e, "delay table");
 }
 

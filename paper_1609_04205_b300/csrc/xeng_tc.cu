@@ -63,6 +63,7 @@ struct JobDev {
     int k_split, tiles_pp, mb, item_begin;
     float vscale;
     int store;            // 1: each visibility written once with plain stores; 0: atomically added
+    const float2 *rot;    // delay compensation a[p][i] (V_ij *= a_i conj(a_j)), or nullptr
 };
 
 struct TcParams {
@@ -328,6 +329,21 @@ __device__ __forceinline__ void flush_tile(const JobDev &J, int p, int i, int jb
     }
     // valid run of this lane: j in [jbase, min(jbase + 32, i + 1)), row i < N
     const int nval = (i < J.N) ? max(0, min(32, i + 1 - jbase)) : 0;
+    if (!exact && J.rot && nval > 0) {
+        // delay compensation (Sec. 4.2.4) folded into the flush: V_ij *= a_i conj(a_j)
+        const float2 *ap = J.rot + (long)p * J.N;
+        const float2 ai = __ldg(ap + i);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (k < nval) {
+                const float2 aj = __ldg(ap + jbase + k);
+                const float wr = ai.x * aj.x + ai.y * aj.y, wi = ai.y * aj.x - ai.x * aj.y;
+                const float vr = __uint_as_float(m[2 * k]), vi = __uint_as_float(m[2 * k + 1]);
+                m[2 * k] = __float_as_uint(vr * wr - vi * wi);
+                m[2 * k + 1] = __float_as_uint(vr * wi + vi * wr);
+            }
+        }
+    }
     if (nval > 0) {
         if (exact) {
             long long *dst = static_cast<long long *>(J.V) + 2 * (prow + jbase);
@@ -886,6 +902,7 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
         D.item_begin = items;
         D.vscale = J.vscale;
         D.store = (J.store && ks == 1) ? 1 : 0;
+        D.rot = J.rot;
         p->slot_of[order[jj]] = jj;
         items += D.tiles_pp * ks * J.n_problems;
         for (int h = 0; h < 2; ++h) {
@@ -955,6 +972,13 @@ cudaError_t tc_plan_set_job(TcPlan *p, int job, long n_time, float vscale, int s
     D.n_time = n_time;
     D.vscale = vscale;
     D.store = (store && D.k_split == 1) ? 1 : 0;
+    return cudaSuccess;
+}
+
+cudaError_t tc_plan_set_rot(TcPlan *p, int job, const float2 *rot)
+{
+    if (job < 0 || job >= p->params.n_jobs) return cudaErrorInvalidValue;
+    p->params.jobs[p->slot_of[job]].rot = rot;
     return cudaSuccess;
 }
 

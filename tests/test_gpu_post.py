@@ -75,6 +75,33 @@ def test_delay_in_context_matches_oracle():
     c.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_delay_in_context_fused_in_tensor_core_flush(variant):
+    """Split-FP16 context (tensor-core X-engine, one SM or SM pairs per tile)
+    with acf_set_delays: the rotation is applied in the X-engine's flush to
+    every push of a two-push integration (linear, so the integrated V is the
+    compensated sum); against the oracle correlator + compensation."""
+    acf = _acf()
+    rng = np.random.default_rng(21 + variant)
+    N, C, P, S = 40, 16, 16, 16 * 16 * 12
+    x = rng.integers(-60, 60, size=(1, 2 * S, N, 2)).astype(np.int8)
+    d = rng.uniform(-3e-6, 3e-6, N)
+    fc = [301 * FS]
+    c = acf.Correlator(N, 1, C, P, 2, "fp16x3", "ci8", S, variant=variant)
+    c.set_delays(d, fc, FS)
+    xd = torch.from_numpy(x).cuda()
+    c.push(xd[:, :S].contiguous())
+    assert c.visibilities() is None
+    c.push(xd[:, S:].contiguous())
+    out = c.empty_visibilities()
+    assert c.visibilities(out) is not None
+    got = _from_dev(out)[0]
+    ref = oracle.correlator(x[0], P, C, push_sizes=[S, S], n_integrate=2)[0]
+    want = post.delay_compensate(ref[None], d, fc, FS)[0]
+    assert norm_err(got, want, N) < 1e-5
+    c.close()
+
+
 def test_set_delays_rejected_for_int8():
     acf = _acf()
     c = acf.Correlator(16, 1, 1, 1, 1, "int8", "ci8", 4096)
@@ -165,7 +192,8 @@ def _flag_case(seed, N, C, n_sb=2):
     return V
 
 
-@pytest.mark.parametrize("N,C,k1,k2", [(40, 16, 5.0, 3.0), (101, 8, 3.0, 2.5), (64, 64, 4.0, 2.0)])
+@pytest.mark.parametrize("N,C,k1,k2", [(40, 16, 5.0, 3.0), (101, 8, 3.0, 2.5), (64, 64, 4.0, 2.0),
+                                       (20, 256, 4.0, 2.5), (33, 100, 3.5, 2.5)])
 def test_sigma_clip_matches_oracle(N, C, k1, k2):
     acf = _acf()
     V = _flag_case(80 + N, N, C)
@@ -178,6 +206,31 @@ def test_sigma_clip_matches_oracle(N, C, k1, k2):
     assert got.sum() > 0
     i, j = post.pairs(N)
     assert not got[..., i == j].any()
+
+
+@pytest.mark.parametrize("N,C", [(24, 16), (25, 80)])
+def test_sigma_clip_threshold_ties_settled_in_fp64(N, C):
+    """Every |V|^2 equal to its threshold, or within the fp32 guard band of
+    it: with k1 = k2 = 1 and a constant V = 0.75 + 1j (|V|^2 = 1.5625, exact
+    in fp32 and fp64) each channel mean equals every element, so every test
+    is a tie that only the fp64 comparison (a > a is false) settles.  One
+    element is raised by 2^-22 in its real part (relative change ~2^-22, well
+    inside the band); a second, large element in the same channel lifts that
+    channel's stage-1 threshold clear of it, so stage 2 must flag it through
+    the fp64 path.  Odd NB (N = 25) takes the scalar sums path."""
+    acf = _acf()
+    i, j = post.pairs(N)
+    cross = np.nonzero(i != j)[0]
+    V = np.full((1, C, i.size), 0.75 + 1.0j, dtype=np.complex64)
+    x, y = cross[5], cross[9]
+    V[0, 4, x] = np.float32(0.75 + 2.0 ** -22) + 1.0j
+    V[0, 4, y] = 30.0 + 40.0j
+    got = acf.postproc.sigma_clip(_to_dev(V), 1.0, 1.0).cpu().numpy()
+    want = post.sigma_clip(V.astype(np.complex128), 1.0, 1.0)
+    assert np.array_equal(got, want)
+    expect = np.zeros_like(want)
+    expect[0, 4, x] = expect[0, 4, y] = 1
+    assert np.array_equal(got, expect)
 
 
 def test_sigma_clip_rejects_bad_threshold():
