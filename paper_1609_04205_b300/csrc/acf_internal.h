@@ -118,7 +118,8 @@ bool tc_supported(int device);
 cudaError_t launch_gain(const float2 *R, const float2 *V, const float2 *g, int N, int C,
                         float *loss, float2 *grad, float *partials, long long n_partials_cap,
                         cudaStream_t s);
-// Loss partials a gain launch needs (64-bit: ceil(N/64)(ceil(N/64)+1)/2 * C).
+// Loss partials a gain launch needs (64-bit): one per block, a block covering a
+// 16 x 64 tile of the triangle for 4 channels: 2 m (m + 1) * ceil(C / 4), m = ceil(N / 64).
 long long gain_partials_needed(int N, int C);
 
 // ---- post-correlation steps (post.cu) ------------------------------------------

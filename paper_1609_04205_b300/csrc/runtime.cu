@@ -706,8 +706,10 @@ static acf_status gain_common(const void *R, const void *V, const void *g, int N
                               cudaStream_t s)
 {
     if (!R || !V || !g || N < 1 || C < 1 || C > 65535) return ACF_EINVAL;
+    // element offsets within one channel's triangle are 32-bit (this also
+    // bounds the tile count, which fills grid x)
+    if ((long long)N * (N + 1) / 2 > 0x7fffffffLL) return ACF_EINVAL;
     const long long need = gain_partials_needed(N, C);
-    if ((need / C) > 0x7fffffffLL) return ACF_EINVAL;       // tiles of one channel fill grid x
     float *part = nullptr;
     {
         int dev = 0;

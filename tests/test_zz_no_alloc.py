@@ -42,7 +42,7 @@ def test_noalloc_gain_matches_allocating_entry_point():
     L = A.lib()
     t = lambda a: torch.as_tensor(a, dtype=torch.complex64, device="cuda").contiguous()
     s = A.stream_handle()
-    for call, (N, C) in enumerate([(96, 3), (200, 8)]):        # two calls in a row: 18, then 80 partials
+    for call, (N, C) in enumerate([(96, 3), (200, 8)]):        # two calls in a row: 12, then 80 partials
         R, V, g = _problem(N, C, 80 + call)
         Rt, Vt, gt = t(R), t(V), t(g)
         loss_a = torch.empty((), dtype=torch.float32, device="cuda")
