@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libacf.so")
-SOURCES = ["chan_ppf.cu", "chan_fast.cu", "chan_ws.cu", "xeng_simt.cu", "xeng_tc.cu", "gain.cu", "post.cu", "runtime.cu", "batch.cu"]
+SOURCES = ["chan_ppf.cu", "chan_fast.cu", "chan_ws.cu", "chan256.cu", "xeng_simt.cu", "xeng_tc.cu", "gain.cu", "post.cu", "runtime.cu", "batch.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -46,6 +46,12 @@ bool chan_fast_supported(acf_in_dtype dt, int C, int P);
 cudaError_t launch_chan_fast(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
                              int n_sb, int N, int C, const float *h, const float *bp, const float2 *tw, int out_kind,
                              void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
+// 256-channel, 16-tap channeliser (chan256.cu): ci8 / ci16 input, history
+// included, operand rows padded to a multiple of 16 spectra.
+bool chan256_supported(acf_in_dtype dt, int C, int P, long t_stride);
+cudaError_t launch_chan256(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
+                           int n_sb, int N, const float *h, const float *bp, const float2 *tw, int out_kind,
+                           void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
 // Warp-specialised 64-channel, 16-tap channeliser (chan_ws.cu): ci8 / ci16
 // input read through a TMA tensor map (N a multiple of 16 bytes' worth of
 // inputs, 16-byte aligned samples).  It produces spectra

@@ -456,6 +456,9 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
         return launch_chan_ws(samples, n_samples, n_hist, dt, n_sb, N, h, bandpass, scale, out_kind, out, out_lo,
                               t_stride, T, s);
     }
+    if (chan256_supported(dt, C, P, t_stride))
+        return launch_chan256(hist, n_hist, samples, n_samples, dt, n_sb, N, h, bandpass, tw, out_kind, out, out_lo,
+                              t_stride, scale, T, s);
     if (chan_fast_supported(dt, C, P))
         return launch_chan_fast(hist, n_hist, samples, n_samples, dt, n_sb, N, C, h, bandpass, tw, out_kind, out,
                                 out_lo, t_stride, scale, T, s);

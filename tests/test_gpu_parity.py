@@ -71,16 +71,19 @@ def test_channelise_fp16_split_reconstructs():
     assert err <= 1e-6 * ref.abs().max().item() * 4
 
 
+@pytest.mark.parametrize("C", [64, 256])
 @pytest.mark.parametrize("dtype,N", [("ci16", 36), ("ci8", 40)])
 @pytest.mark.parametrize("n_hist", [0, 500, 1023, 3000])
-def test_channelise_64ch_history_and_segments_vs_oracle(dtype, N, n_hist):
-    """The warp-specialised 64-channel path (N a multiple of one 16-byte row
-    of inputs): spectra whose windows reach into the history come from the
-    generic kernel, the rest from the TMA-fed kernel, split into several time
-    segments per (subband, input group); two subbands; f32 output against the
-    oracle on the concatenated stream, zeroed tail."""
+def test_channelise_fast_paths_history_and_segments_vs_oracle(C, dtype, N, n_hist):
+    """The 64-channel warp-specialised path (N a multiple of one 16-byte row
+    of inputs: spectra whose windows reach into the history come from the
+    generic kernel, the rest from the TMA-fed kernel) and the 256-channel path
+    (history read in place), split into several time segments per (subband,
+    input); two subbands; f32 output against the oracle on the concatenated
+    stream, zeroed tail."""
     _dev()
-    C, P, S, n_sb = 64, 16, 64 * 700 + 37, 2
+    P, n_sb = 16, 2
+    S = 64 * 700 + 37 if C == 64 else 256 * 150 + 37
     sig = 512.0 if dtype == "ci16" else 16.0
     full = _samples(N, n_hist + S, n_sb, dtype, sigma=sig, seed=60 + n_hist)
     hist = full[:, :n_hist].contiguous() if n_hist else None
@@ -97,13 +100,15 @@ def test_channelise_64ch_history_and_segments_vs_oracle(dtype, N, n_hist):
         assert np.all(got[:, :, T:(T + 63) // 64 * 64] == 0)
 
 
+@pytest.mark.parametrize("C", [64, 256])
 @pytest.mark.parametrize("dtype,N", [("ci16", 48), ("ci8", 64)])
-def test_channelise_64ch_fp16_outputs_and_bandpass(dtype, N):
-    """fp16 and split fp16 outputs of the 64-channel path with non-uniform
-    bandpass weights and an output scale: hi is the fp16 rounding of the
-    scaled fp32 value and hi + lo reconstructs it to fp32 accuracy."""
+def test_channelise_fast_paths_fp16_outputs_and_bandpass(C, dtype, N):
+    """fp16 and split fp16 outputs of the 64- and 256-channel paths with
+    non-uniform bandpass weights and an output scale: hi is the fp16 rounding
+    of the scaled fp32 value and hi + lo reconstructs it to fp32 accuracy."""
     _dev()
-    C, P, S = 64, 16, 64 * 300 + 5
+    P = 16
+    S = 64 * 300 + 5 if C == 64 else 256 * 70 + 5
     sig = 512.0 if dtype == "ci16" else 16.0
     x = _samples(N, S, 2, dtype, sigma=sig, seed=70)
     w = synth.bandpass_ripple(C, 9)
@@ -125,12 +130,14 @@ def test_channelise_64ch_fp16_outputs_and_bandpass(dtype, N):
     assert (Xh[..., T:] == 0).all() and (Xl3[..., T:] == 0).all()
 
 
-def test_correlator_64ch_streaming_pushes_ci16():
-    """Context path over five ragged pushes (history carried by the generic
-    head of each push, the rest by the TMA-fed kernel), integrations of two
+@pytest.mark.parametrize("C", [64, 256])
+def test_correlator_streaming_pushes_ci16(C):
+    """Context path over five ragged pushes (64 channels: history carried by
+    the generic head of each push, the rest by the TMA-fed kernel; 256
+    channels: one kernel reading the history in place), integrations of two
     pushes, split FP16, against the oracle's stream partition."""
     _dev()
-    N, C, P = 44, 64, 16
+    N, P = 44, 16
     pushes = [5000, 1300, 64 * 40 + 7, 260, 9000]
     S = sum(pushes)
     sky = synth.make_sky(N, 2, (0.1, 0.4), 77)
