@@ -187,6 +187,14 @@ def norm_err(V, R, n):
     return float(np.max(np.abs(V - R) / np.sqrt(auto[:, i] * auto[:, j])))
 
 
+def xeng_desc(t):
+    """Kernel and launch shape of an X-engine tuning (acf_query_xengine)."""
+    if not t:
+        return "k_xeng_simt"
+    kern = "k_xeng_tc2: SM pairs per 256x256 tile" if t["variant"] else "k_xeng_tc: one SM per 128x%d tile" % t["n_tile"]
+    return "%s, time split %d, %s" % (kern, t["k_split"], "autotuned" if t["tuned"] else "creation rule")
+
+
 def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None, keep=None):
     """Steps of the whole stage in one precision mode; returns dict with timings.
     keep(out) -> host copy of the part of the last step's visibilities the
@@ -194,6 +202,9 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None, keep=No
     N, n_sb, C, P = w["n_inputs"], w["n_subbands"], w["n_channels"], w["n_taps"]
     S = w["n_samples"]
     c = acf.Correlator(N, n_sb, C, P, 1, mode, w["dtype"], S)
+    # the context's autotuner picks the X-engine launch shape on this geometry
+    # (untimed, before the warm-up); the FP32 comparison path has none
+    tuning = c.tune() if mode != "fp32" else None
     c.enable_timing(True)
     out = c.empty_visibilities()
     Ts, chan_ms, xeng_ms = [], [], []
@@ -224,7 +235,7 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None, keep=No
     return dict(ms_per_step=total_ms / steps, tops=ops / (total_ms * 1e-3) / 1e12, T=Ts,
                 chan_ms=statistics.median(chan_ms), xeng_ms=statistics.median(xeng_ms),
                 xeng_tops=xops(N, statistics.median(Ts), C, n_sb) / (statistics.median(xeng_ms) * 1e-3) / 1e12,
-                launches=launches, ops_per_step=ops / steps, kept=kept, pushes=warmup + steps)
+                launches=launches, ops_per_step=ops / steps, kept=kept, pushes=warmup + steps, xengine_tuning=tuning)
 
 
 def time_post(acf, torch, pk, N, n_sb, C, oracle_sample=True):
@@ -403,12 +414,35 @@ def profile_case(mode):
     sky = synth.make_sky(w["n_inputs"], w["n_sources"], w["flux"], w["seed"]) if w["n_sources"] else None
     x = synth.voltages(w["n_inputs"], w["n_samples"], 1, w["dtype"], w["sigma"], sky, w["seed"], device="cuda")
     with acf.Correlator(w["n_inputs"], 1, w["n_channels"], w["n_taps"], 1, mode, w["dtype"], w["n_samples"]) as c:
+        if mode != "fp32":
+            c.tune()
         out = c.empty_visibilities()
         for _ in range(4):
             c.push(x)
             c.visibilities(out)
         torch.cuda.synchronize()
     print("profile case %s done" % mode)
+    return 0
+
+
+def probe():
+    """The tensor-pipe ceiling with resident operands, beside the measured
+    cuBLAS peaks: how far above the copy-bound denominators the MMA units
+    themselves go.  Clocks are sampled during the runs."""
+    import torch
+
+    import paper_1609_04205_b300 as acf
+    pk = peaks()
+    acf.probe_tensor_peak(8192)                      # warm the clocks and the module
+    clk = Clocks(0)
+    runs = [acf.probe_tensor_peak(65536) for _ in range(60)]      # ~1 s under the clock sampler
+    clocks = clk.stop()
+    best = max(r["tflops"] for r in runs)
+    print(json.dumps(dict(probe="tcgen05 kind::f16 M128 N256 K16, operands resident in shared memory, one CTA per SM",
+                          tflops_median=statistics.median(r["tflops"] for r in runs), ms_median=statistics.median(
+                              r["ms"] for r in runs), best_tflops=best, runs=len(runs),
+                          vs_measured_bf16_burst=best / pk["bf16"], vs_measured_bf16_sustained=best / pk["bf16_sus"],
+                          nominal_dense_fp16_tflops=2250.0, clocks=clocks, torch=torch.__version__)))
     return 0
 
 
@@ -437,6 +471,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the comparison modes and the e2e pass")
     ap.add_argument("--post-case", action="store_true",
                     help="run only the post-correlation kernels on the A-12 visibility set (profiling)")
+    ap.add_argument("--probe", action="store_true",
+                    help="tensor-pipe rate with operands resident in shared memory (one JSON line), then exit")
     ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8"], default=None,
                     help="small case for ncu captures: one subband of the default workload (one raw "
                          "A-6 subband for int8), warm-up plus three pushes, no JSON line")
@@ -445,6 +481,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return profile_case(args.profile_case)
+    if args.probe:
+        return probe()
     if args.post_case:
         return post_case()
 
@@ -485,7 +523,7 @@ def main():
     if not args.quick:
         r3 = time_mode(acf, torch, x, w, "fp16x3", max(2, args.steps // 2), 2, stream, keep=keep_a12)
         extra["fp16x3"] = dict(tops=r3["tops"], xeng_tops=r3["xeng_tops"], ms_per_step=r3["ms_per_step"],
-                               issued_tensor_tops=3 * r3["xeng_tops"])
+                               issued_tensor_tops=3 * r3["xeng_tops"], xengine_tuning=r3["xengine_tuning"])
         r32 = time_mode(acf, torch, x, w, "fp32", 2, 1, stream, keep=keep_a12)
         fp32_peak = fp32_fma_peak_tflops(torch, pk["sm_max_mhz"])
         extra["fp32_cuda_core"] = dict(tops=r32["tops"], xeng_tops=r32["xeng_tops"], ms_per_step=r32["ms_per_step"],
@@ -504,6 +542,7 @@ def main():
                        keep=lambda out: out[0, 0, :nb64].cpu().numpy())
         x6_sub = x6[0][:, :INT8_ACC_INPUTS].cpu().numpy()
         extra["int8_raw_a6"] = dict(tops=r8["tops"], xeng_tops=r8["xeng_tops"], ms_per_step=r8["ms_per_step"],
+                                    xengine_tuning=r8["xengine_tuning"],
                                     frac_of_fp16_sustained=r8["xeng_tops"] / pk["bf16_sus"],
                                     note="exact INT8 runs on the fp16 tensor path (kind::i8 does not assemble "
                                          "for sm_103a), so its peak is the fp16 one",
@@ -522,6 +561,7 @@ def main():
         try:
             xh = x.cpu().pin_memory()
             c = acf.Correlator(N, n_sb, w["n_channels"], w["n_taps"], 1, "fp16", w["dtype"], S)
+            c.tune()
             outh = torch.empty((n_sb, w["n_channels"], N * (N + 1) // 2, 2), dtype=torch.float32).pin_memory()
             with torch.cuda.stream(stream):
                 for _ in range(2):
@@ -579,10 +619,11 @@ def main():
     tps = xeng_traffic_per_subband()
     roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16_sus"], unit="TFLOP/s",
                 frac=achieved / pk["bf16_sus"], traffic=None if tps is None else tps * n_sb,
-                note="X-engine (k_xeng_tc2: SM pairs per 256x256 tile, FP16 operands, fp32 accumulation); algorithmic ops "
+                note="X-engine (%s, FP16 operands, fp32 accumulation); algorithmic ops "
                      "8*N(N+1)/2*spectra*channels*subbands = %.3e per launch over its CUDA-event time %.3f ms; "
                      "peak = %s bf16 sustained (fp16 dense = bf16 dense on B300); frac of burst %.3f"
-                     % (main_r["ops_per_step"], xeng_ms, pk["src"], achieved / pk["bf16"]))
+                     % (xeng_desc(main_r["xengine_tuning"]), main_r["ops_per_step"], xeng_ms, pk["src"],
+                        achieved / pk["bf16"]))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="fp16",
                 data="synthetic",
@@ -591,6 +632,7 @@ def main():
                             global_batch=n_sb * world, l2="inputs 14.4 GB > L2 (no flush needed)",
                             parallelism="independent subband sets per rank" if world > 1 else "single GPU"),
                 roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
+                xengine_tuning=main_r["xengine_tuning"],
                 channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
                                  bytes=in_bytes + out_bytes),
                 e2e=e2e, cpu_baseline=cpu, accuracy=accuracy, modes=extra, post=post_r, ragged_batch=batch_r,

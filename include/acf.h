@@ -152,6 +152,30 @@ acf_status acf_last_timing(acf_ctx *ctx, float *chan_ms, float *xeng_ms);
  * values, ESTATE mid-integration or in FP32 mode. */
 acf_status acf_set_xengine_variant(acf_ctx *ctx, int variant);
 
+/* Autotune the tensor-core X-engine on this context's geometry: times every
+ * candidate launch shape (variant 0 or 1, N tile 128 or 256 real rows, time
+ * split 1, 2 or 4) on the context's full launch (its first subband's
+ * problems when the scratch for all of them cannot be had), writing a
+ * temporary visibility buffer (allocated and freed here), and rebuilds the
+ * launch plan with the fastest.  Only between integrations (ESTATE
+ * otherwise, and in FP32 mode); ENOMEM when the scratch cannot be had.
+ * Synchronises the device. */
+acf_status acf_tune(acf_ctx *ctx);
+
+/* Measurement aid with no counterpart in the paper: the tensor pipe's rate
+ * with operands resident in shared memory.  Every SM runs one CTA issuing
+ * k_steps x 4 back-to-back kind::f16 MMAs (M = 128, N = 256, K = 16, fp32
+ * accumulation in TMEM) on fixed tiles; no global memory is read.  Writes the
+ * achieved TFLOP/s (2 M N K per MMA) and the launch time in ms (host
+ * pointers, either may be NULL).  k_steps in [1, 2^22]; EUNSUPPORTED without
+ * an sm_103 device.  Allocates a few bytes; synchronises the device. */
+acf_status acf_probe_tensor_peak(long k_steps, double *tflops, float *ms);
+
+/* The X-engine launch shape in use: variant (0 / 1), N tile, time split, and
+ * whether acf_tune chose it (1) or the creation rule did (0).  Any pointer
+ * may be NULL. */
+acf_status acf_query_xengine(const acf_ctx *ctx, int *variant, int *n_tile, int *k_split, int *tuned);
+
 /* Release every resource.  Synchronises the device first.  NULL is a no-op. */
 acf_status acf_destroy(acf_ctx *ctx);
 

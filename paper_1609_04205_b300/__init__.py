@@ -7,6 +7,6 @@ libacf.so raises instead of falling back.
 """
 from ._lib import AcfError, lib  # noqa: F401
 from .correlator import (Batch, Correlator, channelise, device_status, launch_count,  # noqa: F401
-                         n_baselines, prototype, transpose_raw, xengine)
+                         n_baselines, probe_tensor_peak, prototype, transpose_raw, xengine)
 from .gain import GainCorr, gain_grad, gain_loss_and_grad  # noqa: F401
 from . import postproc  # noqa: F401

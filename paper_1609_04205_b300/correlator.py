@@ -66,6 +66,19 @@ class Correlator:
         """0: one SM per tile; 1: SM pairs sharing each 256x256 tile (cta_group::2)."""
         A.check(self._L.acf_set_xengine_variant(self._h, int(variant)), self._h)
 
+    def tune(self):
+        """Time every X-engine launch shape on this geometry and keep the
+        fastest (acf_tune); only between integrations.  Returns xengine_tuning()."""
+        A.check(self._L.acf_tune(self._h), self._h)
+        return self.xengine_tuning()
+
+    def xengine_tuning(self) -> dict:
+        """The X-engine launch shape in use (acf_query_xengine)."""
+        v, nt, ks, tu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        A.check(self._L.acf_query_xengine(self._h, ctypes.byref(v), ctypes.byref(nt), ctypes.byref(ks),
+                                          ctypes.byref(tu)), self._h)
+        return dict(variant=v.value, n_tile=nt.value, k_split=ks.value, tuned=bool(tu.value))
+
     def set_delays(self, delays, f_centre, sample_rate: float):
         """Delay-compensate every integration handed out from now on (acf_set_delays);
         delays=None switches it off."""
@@ -231,6 +244,14 @@ class Batch:
 
 def launch_count() -> int:
     return int(A.lib().acf_launch_count())
+
+
+def probe_tensor_peak(k_steps: int = 16384) -> dict:
+    """Tensor-pipe rate with operands resident in shared memory
+    (acf_probe_tensor_peak): kind::f16 MMAs M = 128, N = 256 on every SM."""
+    tf, ms = ctypes.c_double(), ctypes.c_float()
+    A.check(A.lib().acf_probe_tensor_peak(int(k_steps), ctypes.byref(tf), ctypes.byref(ms)), None)
+    return dict(tflops=tf.value, ms=ms.value, k_steps=int(k_steps))
 
 
 def device_status() -> int:

@@ -118,6 +118,9 @@ int tc_plan_job_stores(const TcPlan *p, int job);   // 1 when the job overwrites
 int tc_plan_job_split(const TcPlan *p, int job);
 int tc_plan_items(const TcPlan *p);
 void tc_plan_destroy(TcPlan *p);
+// Tensor-pipe ceiling with resident operands (xeng_tc.cu): kind::f16 MMAs
+// M = 128, N = 256 on every SM for k_steps K steps of 64; TFLOP/s and ms.
+cudaError_t probe_tensor_peak(long k_steps, double *tflops, float *ms);
 bool tc_supported(int device);
 
 // ---- gain (gain.cu) ---------------------------------------------------------

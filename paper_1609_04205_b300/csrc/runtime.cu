@@ -68,6 +68,8 @@ struct acf_ctx {
     std::vector<cudaEvent_t> ev_copied;
     TcPlan *plan = nullptr;
     int variant = 0;              // 0: one SM per 128x256 tile; 1: SM pairs per 256x256 tile
+    TcTuning tun;                 // N tile, time split, order (pair mirrors `variant`)
+    bool tuned = false;           // tun chosen by acf_tune
     int pushes = 0;
     bool ready = false;
     bool v_valid = false;         // V already holds this integration's partial sums
@@ -150,9 +152,28 @@ static cudaError_t make_plan(acf_ctx *c, std::string *perr)
     j.mode = c->mode;
     j.vscale = 1.f / (c->scale * c->scale);
     j.rot = c->d_delay_tab;
-    TcTuning tun;
+    TcTuning tun = c->tun;
     tun.pair = c->variant;
+    if (tun.pair) tun.n_tile = 256;     // the pair kernel always uses 256-row tiles
     return tc_plan_create(&j, 1, tun, &c->plan, perr);
+}
+
+// X-engine launch of the context's geometry restricted to its first
+// n_problems problems, into scratch V: the autotuner's timing job.
+static TcJob timing_job(const acf_ctx *c, int n_problems, void *V)
+{
+    const long L = (long)c->P * c->C;
+    TcJob j;
+    j.x = static_cast<const __half *>(c->d_X);
+    j.x_lo = static_cast<const __half *>(c->d_Xlo);
+    j.V = V;
+    j.N = c->N;
+    j.n_problems = n_problems;
+    j.n_time = c->C == 1 ? c->max_samples : spectra_for(L - 1 + c->max_samples, c->P, c->C);
+    j.t_stride = c->t_stride;
+    j.mode = c->mode;
+    j.vscale = 1.f / (c->scale * c->scale);
+    return j;
 }
 
 extern "C" {
@@ -177,6 +198,105 @@ acf_status acf_set_xengine_variant(acf_ctx *c, int variant)
         return fail(c, ACF_ECUDA, "tensor-core plan: " + perr);
     }
     return ACF_OK;
+}
+
+acf_status acf_tune(acf_ctx *c)
+{
+    if (!c) return ACF_EINVAL;
+    if (c->mode == ACF_X_FP32) return fail(c, ACF_ESTATE, "the FP32 path has no tensor-core plan");
+    if (c->pushes != 0) return fail(c, ACF_ESTATE, "tuning only between integrations");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    // time the context's whole launch (how its tiles spread over the SMs
+    // decides between the shapes), writing a scratch V; when that does not
+    // fit, the first subband's problems
+    int n_prob = c->n_sb * c->C;
+    void *V = nullptr;
+    size_t vb = 0;
+    for (;;) {
+        vb = (size_t)n_prob * n_baselines(c->N) * (c->mode == ACF_X_INT8 ? 16 : 8);
+        if ((e = cudaMalloc(&V, vb)) == cudaSuccess) break;
+        cudaGetLastError();
+        if (n_prob == c->C) return cuda_fail(c, e, "tuning scratch");
+        n_prob = c->C;
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    TcJob j = timing_job(c, n_prob, V);
+    float best = 1e30f;
+    TcTuning best_t = c->tun;
+    best_t.pair = c->variant;
+    for (int pair : {1, 0})
+        for (int nt : {256, 128})
+            for (int ks : {1, 2, 4}) {
+                if (pair && nt == 128) continue;
+                TcTuning t;
+                t.pair = pair;
+                t.n_tile = nt;
+                t.k_split = ks;
+                TcPlan *p = nullptr;
+                std::string perr;
+                if (tc_plan_create(&j, 1, t, &p, &perr) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                tc_plan_set_job(p, 0, j.n_time, j.vscale, ks == 1 ? 1 : 0);
+                // a time split accumulates atomically, so a push must clear V
+                // first: that clear is part of the candidate's cost
+                const bool clears = !tc_plan_job_stores(p, 0);
+                if (clears) cudaMemsetAsync(V, 0, vb, st);
+                tc_plan_launch(p, st);                       // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r) {
+                    if (clears) cudaMemsetAsync(V, 0, vb, st);
+                    tc_plan_launch(p, st);
+                }
+                cudaEventRecord(e1, st);
+                float ms = 0.f;
+                const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                tc_plan_destroy(p);
+                if (!ok) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_t = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(V);
+    if (best >= 1e30f) return fail(c, ACF_ECUDA, "no X-engine candidate ran");
+    c->tun = best_t;
+    c->variant = best_t.pair;
+    c->tuned = true;
+    std::string perr;
+    if ((e = make_plan(c, &perr)) != cudaSuccess) return fail(c, ACF_ECUDA, "tensor-core plan: " + perr);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(c, e, "tune");
+    return ACF_OK;
+}
+
+acf_status acf_query_xengine(const acf_ctx *c, int *variant, int *n_tile, int *k_split, int *tuned)
+{
+    if (!c) return ACF_EINVAL;
+    if (variant) *variant = c->variant;
+    if (n_tile) *n_tile = c->variant ? 256 : c->tun.n_tile;
+    if (k_split) *k_split = c->tun.k_split;
+    if (tuned) *tuned = c->tuned ? 1 : 0;
+    return ACF_OK;
+}
+
+acf_status acf_probe_tensor_peak(long k_steps, double *tflops, float *ms)
+{
+    if (k_steps < 1 || k_steps > (1L << 22)) return ACF_EINVAL;
+    cudaError_t e = probe_tensor_peak(k_steps, tflops, ms);
+    if (e == cudaErrorInvalidDevice) return ACF_EUNSUPPORTED;
+    return e == cudaSuccess ? ACF_OK : ACF_ECUDA;
 }
 
 long long acf_launch_count(void) { return g_launches.load(); }

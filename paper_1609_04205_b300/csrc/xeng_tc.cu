@@ -1010,6 +1010,121 @@ cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-pipe ceiling probe: every SM runs one CTA whose elected thread issues
+// back-to-back kind::f16 MMAs (M = 128, N = 256, K = 16) on A (128 x 64) and
+// B (256 x 64) fp16 tiles resident in shared memory, accumulating in TMEM, so
+// no operand traffic limits the rate.  The operands hold small non-zero
+// values (the power drawn, and so the clock, depends on the data).  One
+// commit at the end; the wait for it is bounded (kWaitCycles), a timeout sets
+// *err.  One lane reads the accumulator back so the work stays observable.
+namespace {
+constexpr int kProbeThreads = 128;
+constexpr uint32_t kProbeCols = 256;
+
+__global__ void __launch_bounds__(kProbeThreads, 1) k_probe_mma(long k_steps, int *err, float *sink)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t done;
+    __shared__ uint32_t tmem_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __half *ab = reinterpret_cast<__half *>(smem);
+    constexpr int kElems = (kBM + 256) * kBK;            // A then B, one K step of 64
+    for (int i = threadIdx.x; i < kElems; i += kProbeThreads) {
+        const uint32_t hsh = (uint32_t)(i + 1) * 2654435761u;
+        ab[i] = __float2half(((float)((hsh >> 20) & 63) - 31.5f) * (1.f / 64.f));
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                     "r"(kProbeCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_s;
+    if (threadIdx.x == 0) {
+        const uint32_t a = smem_u32(smem);
+        const uint64_t da = desc_sw128(a), db = desc_sw128(a + kBM * kBK * 2);
+        const uint32_t idesc = idesc_f16(256);
+        for (long s = 0; s < k_steps; ++s) {
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+                mma_f16(tmem, da + 2 * kk, db + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&done));
+        const long long t0 = clock64();
+        bool ok = true;
+        while (!mbar_try_wait(smem_u32(&done), 0)) {
+            if (clock64() - t0 > kWaitCycles) {
+                atomicCAS(err, 0, 21);
+                ok = false;
+                break;
+            }
+        }
+        (void)ok;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        uint32_t r[32];
+        tmem_ld32(tmem, r);
+        tmem_wait_ld();
+        if (lane == 0) sink[blockIdx.x] = __uint_as_float(r[0]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kProbeCols) : "memory");
+    }
+}
+}  // namespace
+
+cudaError_t probe_tensor_peak(long k_steps, double *tflops, float *ms_out)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (!tc_supported(dev)) return cudaErrorInvalidDevice;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)(kBM + 256) * kBK * 2 + 1024;
+    if ((e = cudaFuncSetAttribute(k_probe_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    float *sink = nullptr;
+    int *err = device_error_word();
+    if (!err) return cudaErrorMemoryAllocation;
+    if ((e = cudaMalloc(&sink, sizeof(float) * sms)) != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_probe_mma<<<sms, kProbeThreads, smem>>>(std::max<long>(1, k_steps / 8), err, sink);   // warm-up
+    g_launches++;
+    cudaEventRecord(e0);
+    k_probe_mma<<<sms, kProbeThreads, smem>>>(k_steps, err, sink);
+    g_launches++;
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * kBM * 256 * 16 * (kBK / 16) * (double)k_steps * sms;
+    if (tflops) *tflops = flops / (ms * 1e-3) / 1e12;
+    if (ms_out) *ms_out = ms;
+    return cudaSuccess;
+}
+
 int tc_plan_items(const TcPlan *p) { return p->params.n_items; }
 void tc_plan_destroy(TcPlan *p) { delete p; }
 
