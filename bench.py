@@ -402,11 +402,54 @@ def aggregate(ms_local, ops_local, device="cpu"):
     return ms, float(tot[1].item()) / (ms * 1e-3) / 1e12
 
 
+def profile_case_kernels(which):
+    """Small cases of single kernels for ncu captures (a few GB on the device):
+    sigma_clip -- acf_sigma_clip on four A-12 subbands of visibilities (1.36 GB);
+    gain -- acf_gain_forward on 576 inputs x 64 channels;
+    chan256 -- acf_channelise, 256 channels x 16 taps, 1152 inputs x 48,828 ci8
+    samples to split fp16.  Four calls each."""
+    import ctypes
+
+    import torch
+
+    import paper_1609_04205_b300 as acf
+    from paper_1609_04205_b300 import _lib as A
+    L = A.lib()
+    hs = A.stream_handle(None)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    if which == "sigma_clip":
+        N, n_sb, C = 1152, 4, 64
+        V = torch.randn((n_sb, C, N * (N + 1) // 2, 2), generator=g, device="cuda")
+        flags = torch.empty((n_sb, C, N * (N + 1) // 2), dtype=torch.uint8, device="cuda")
+        for _ in range(4):
+            A.check(L.acf_sigma_clip(A.ptr(V), A.ptr(flags), n_sb, C, N, 5.0, 3.0, hs))
+    elif which == "gain":
+        time_gain(acf, torch, peaks(), steps=1)
+    elif which == "chan256":
+        N, S, C, P = 1152, 48828, 256, 16
+        x = torch.randint(-100, 100, (1, S, N, 2), dtype=torch.int8, device="cuda", generator=g)
+        T = (S - (P - 1) * C) // C
+        ts = (T + 63) // 64 * 64
+        X = torch.empty((1, C, 2 * N, ts), dtype=torch.float16, device="cuda")
+        Xl = torch.empty_like(X)
+        h = torch.as_tensor(acf.prototype(P, C), device="cuda")
+        bp = torch.ones(C, device="cuda")
+        To = ctypes.c_long()
+        for _ in range(4):
+            A.check(L.acf_channelise(None, 0, A.ptr(x), S, A.DTYPES["ci8"], 1, N, C, P, A.ptr(h), A.ptr(bp), 2,
+                                     A.ptr(X), A.ptr(Xl), ts, 0.25, ctypes.byref(To), hs))
+    torch.cuda.synchronize()
+    print("profile case %s done" % which)
+    return 0
+
+
 def profile_case(mode):
     import torch
 
     import paper_1609_04205_b300 as acf
     import synth
+    if mode in ("sigma_clip", "gain", "chan256"):
+        return profile_case_kernels(mode)
     w = dict(synth.WORKLOADS["a6" if mode == "int8" else "a12"])
     w["n_subbands"] = 1
     if mode == "int8":
@@ -473,9 +516,11 @@ def main():
                     help="run only the post-correlation kernels on the A-12 visibility set (profiling)")
     ap.add_argument("--probe", action="store_true",
                     help="tensor-pipe rate with operands resident in shared memory (one JSON line), then exit")
-    ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8"], default=None,
+    ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8", "sigma_clip", "gain", "chan256"],
+                    default=None,
                     help="small case for ncu captures: one subband of the default workload (one raw "
-                         "A-6 subband for int8), warm-up plus three pushes, no JSON line")
+                         "A-6 subband for int8), warm-up plus three pushes; or one post-correlation, gain "
+                         "or 256-channel kernel on a few GB; no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
