@@ -31,11 +31,13 @@ void prototype_host(int P, int C, std::vector<float> &h);
 // ---- channeliser (chan_ppf.cu) -------------------------------------------
 // Twiddle table exp(-2 pi i k / C), k < C, float2, device.
 cudaError_t make_twiddles(int C, float2 **d_tw);
+// scratch: an optional device buffer the 256-channel path may use for its
+// corner turn (chan256_scratch_bytes); other geometries ignore it.
 cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples, long n_samples,
                               acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
                               const float *bandpass, const float2 *tw, int out_kind, void *out,
                               void *out_lo, long t_stride, float scale, long T,
-                              cudaStream_t s);
+                              cudaStream_t s, void *scratch = nullptr, size_t scratch_bytes = 0);
 // General kernel (any supported C, P, dtype); launch_channelise picks the fast path when it applies.
 cudaError_t launch_channelise_generic(const void *hist, long n_hist, const void *samples, long n_samples,
                                       acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
@@ -48,10 +50,16 @@ cudaError_t launch_chan_fast(const void *hist, long n_hist, const void *samples,
                              void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
 // 256-channel, 16-tap channeliser (chan256.cu): ci8 / ci16 input, history
 // included, operand rows padded to a multiple of 16 spectra.
+// With a scratch buffer of chan256_scratch_bytes() it first corner-turns the
+// stream into input-major rows, so that the per-phase sample loads are
+// contiguous; without one it reads the [time][input] stream directly.
 bool chan256_supported(acf_in_dtype dt, int C, int P, long t_stride);
+long chan256_row_pitch(long n_hist, long n_samples);
+size_t chan256_scratch_bytes(acf_in_dtype dt, int n_sb, int N, long n_hist, long n_samples);
 cudaError_t launch_chan256(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
                            int n_sb, int N, const float *h, const float *bp, const float2 *tw, int out_kind,
-                           void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s);
+                           void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s,
+                           void *scratch = nullptr, size_t scratch_bytes = 0);
 // Warp-specialised 64-channel, 16-tap channeliser (chan_ws.cu): ci8 / ci16
 // input read through a TMA tensor map (N a multiple of 16 bytes' worth of
 // inputs, 16-byte aligned samples).  It produces spectra

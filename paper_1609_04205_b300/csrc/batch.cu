@@ -42,6 +42,8 @@ struct acf_batch {
     std::vector<acf_job> jobs;
     std::vector<long> T, t_stride;
     std::vector<void *> X, Xlo;
+    std::vector<void *> cturn;          // per job: 256-channel corner-turn scratch (or null)
+    std::vector<size_t> cturn_bytes;
     std::vector<size_t> v_bytes;
     std::vector<float> scale;
     std::map<long, float *> d_h;        // key P*1024 + C
@@ -113,7 +115,7 @@ static cudaError_t enqueue_all(acf_batch *b, const void *const *inputs, void *co
             e = launch_channelise(nullptr, 0, inputs[k], J.n_samples, ACF_IN_CI8, 1, J.n_inputs, J.n_channels, J.n_taps,
                                   b->d_h[(long)J.n_taps * 1024 + J.n_channels], b->d_bp[J.n_channels],
                                   b->d_tw[J.n_channels], OUT_F16X3, b->X[k], b->Xlo[k], b->t_stride[k], b->scale[k],
-                                  b->T[k], sk);
+                                  b->T[k], sk, b->cturn[k], b->cturn_bytes[k]);
         }
         if (e != cudaSuccess) return e;
     }
@@ -252,6 +254,14 @@ acf_status acf_batch_create(acf_batch **out, const acf_job *jobs, int n_jobs, in
         if (xl) cudaMemset(xl, 0, xb);
         b->T.push_back(T);
         b->t_stride.push_back(ts);
+        void *ct = nullptr;
+        size_t ctb = 0;
+        if (chan256_supported(ACF_IN_CI8, J.n_channels, J.n_taps, ts)) {
+            ctb = chan256_scratch_bytes(ACF_IN_CI8, 1, J.n_inputs, 0, J.n_samples);
+            if ((e = cudaMalloc(&ct, ctb)) != cudaSuccess) return cleanup(ACF_ENOMEM, "corner-turn scratch");
+        }
+        b->cturn.push_back(ct);
+        b->cturn_bytes.push_back(ctb);
         b->v_bytes.push_back((size_t)J.n_channels * n_baselines(J.n_inputs) * (raw ? 16 : 8));
         float sc = 1.f;
         if (!raw) {
@@ -360,6 +370,7 @@ acf_status acf_batch_destroy(acf_batch *b)
     if (b->plan) tc_plan_destroy(b->plan);
     for (void *p : b->X) cudaFree(p);
     for (void *p : b->Xlo) cudaFree(p);
+    for (void *p : b->cturn) cudaFree(p);
     for (auto &kv : b->d_h) cudaFree(kv.second);
     for (auto &kv : b->d_tw) cudaFree(kv.second);
     for (auto &kv : b->d_bp) cudaFree(kv.second);

@@ -19,6 +19,7 @@
 // are staged spectrum-major and each output row (channel, input, re|im) leaves
 // as one run of 16 spectra: 32 bytes in fp16, 64 in fp32, whole sectors.
 #include <algorithm>
+#include <type_traits>
 
 #include "acf_internal.h"
 
@@ -79,11 +80,44 @@ __device__ __forceinline__ void dft16(float2 (&z)[16])
 // entry (q, j) of one spectrum's buffer
 __device__ __forceinline__ int spos(int q, int j) { return 16 * j + (q ^ j); }
 
-template <typename IN, int OUTK>
+// Corner turn of the stream (history, then the push) into input-major rows,
+// out[subband][input][q] with row pitch ld, so that k_chan256 reads each
+// phase's samples as contiguous runs: 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_corner_turn(const T *__restrict__ hist, long n_hist, const T *__restrict__ in, long n_samples, int N,
+              T *__restrict__ out, long ld)
+{
+    __shared__ T tile[32][33];
+    const int sb = blockIdx.z;
+    const long q0 = (long)blockIdx.x * 32;
+    const int n0 = blockIdx.y * 32;
+    const long L = n_hist + n_samples;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const long q = q0 + r;
+        const int n = n0 + tx;
+        T v = T(0);
+        if (q < L && n < N)
+            v = q < n_hist ? hist[((long)sb * n_hist + q) * N + n] : in[((long)sb * n_samples + (q - n_hist)) * N + n];
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int n = n0 + r;
+        const long q = q0 + tx;
+        if (n < N && q < L) out[((long)sb * N + n) * ld + q] = tile[tx][r];
+    }
+}
+
+// IM: samples come from the corner-turned rows xim[subband][input][q] (pitch
+// ld, history included) instead of the [time][input] stream.
+template <typename IN, int OUTK, bool IM>
 __global__ void __launch_bounds__(kC, 1)
 k_chan256(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, long n_samples, int N,
           const float *__restrict__ h, const float *__restrict__ bp, const float2 *__restrict__ tw_g,
-          void *__restrict__ out, void *__restrict__ out_lo, long t_stride, float scale, long T, long m_per_block)
+          void *__restrict__ out, void *__restrict__ out_lo, long t_stride, float scale, long T, long m_per_block,
+          const IN *__restrict__ xim, long ld)
 {
     __shared__ __align__(16) float2 buf[kMB * kC];   // 32 KB: spectra, then the staged results
     __shared__ float2 tw[kC];
@@ -104,9 +138,11 @@ k_chan256(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, l
     const float osc = OUTK == OUT_F32 ? 1.f : scale;
 
     // sample of phase c in spectrum row r (stream index r * 256 + c)
+    const IN *row = IM ? xim + ((long)sb * N + n) * ld : nullptr;
     auto fetch = [&](long r) -> IN {
         const long q = r * kC + c;
         if (q >= stream_len) return IN{};
+        if (IM) return row[q];
         return q < n_hist ? hsb[q * N + n] : isb[(q - n_hist) * N + n];
     };
     float2 w[16];                       // ring: row r in slot r & 15
@@ -239,10 +275,16 @@ k_chan256(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, l
 template <typename IN, int OUTK>
 cudaError_t launch_k(const void *hist, long n_hist, const void *samples, long n_samples, int n_sb, int N,
                      const float *h, const float *bp, const float2 *tw, void *out, void *out_lo, long t_stride,
-                     float scale, long T, long mpb, dim3 grid, cudaStream_t s)
+                     float scale, long T, long mpb, dim3 grid, const void *xim, long ld, cudaStream_t s)
 {
-    k_chan256<IN, OUTK><<<grid, kC, 0, s>>>(static_cast<const IN *>(hist), n_hist, static_cast<const IN *>(samples),
-                                            n_samples, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb);
+    if (xim)
+        k_chan256<IN, OUTK, true><<<grid, kC, 0, s>>>(static_cast<const IN *>(hist), n_hist,
+                                                     static_cast<const IN *>(samples), n_samples, N, h, bp, tw, out,
+                                                     out_lo, t_stride, scale, T, mpb, static_cast<const IN *>(xim), ld);
+    else
+        k_chan256<IN, OUTK, false><<<grid, kC, 0, s>>>(static_cast<const IN *>(hist), n_hist,
+                                                      static_cast<const IN *>(samples), n_samples, N, h, bp, tw, out,
+                                                      out_lo, t_stride, scale, T, mpb, nullptr, 0);
     g_launches++;
     return cudaGetLastError();
 }
@@ -250,17 +292,37 @@ cudaError_t launch_k(const void *hist, long n_hist, const void *samples, long n_
 template <typename IN>
 cudaError_t launch_dt(int out_kind, const void *hist, long n_hist, const void *samples, long n_samples, int n_sb,
                       int N, const float *h, const float *bp, const float2 *tw, void *out, void *out_lo,
-                      long t_stride, float scale, long T, long mpb, dim3 grid, cudaStream_t s)
+                      long t_stride, float scale, long T, long mpb, dim3 grid, void *scratch, cudaStream_t s)
 {
+    long ld = 0;
+    if (scratch) {
+        // corner turn first: [subband][input][q], q over history and push
+        using W = typename std::conditional<sizeof(IN) == 2, uint16_t, uint32_t>::type;
+        ld = chan256_row_pitch(n_hist, n_samples);
+        const long L = n_hist + n_samples;
+        const dim3 g((unsigned)((L + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)n_sb);
+        k_corner_turn<W><<<g, 256, 0, s>>>(static_cast<const W *>(hist), n_hist, static_cast<const W *>(samples),
+                                          n_samples, N, static_cast<W *>(scratch), ld);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     switch (out_kind) {
-    case OUT_F32: return launch_k<IN, OUT_F32>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, s);
-    case OUT_F16: return launch_k<IN, OUT_F16>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, s);
-    case OUT_F16X3: return launch_k<IN, OUT_F16X3>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, s);
+    case OUT_F32: return launch_k<IN, OUT_F32>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, scratch, ld, s);
+    case OUT_F16: return launch_k<IN, OUT_F16>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, scratch, ld, s);
+    case OUT_F16X3: return launch_k<IN, OUT_F16X3>(hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, scratch, ld, s);
     }
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
+
+long chan256_row_pitch(long n_hist, long n_samples) { return round_up(n_hist + n_samples, 16); }
+
+size_t chan256_scratch_bytes(acf_in_dtype dt, int n_sb, int N, long n_hist, long n_samples)
+{
+    return (size_t)n_sb * N * chan256_row_pitch(n_hist, n_samples) * in_elem_bytes(dt);
+}
 
 bool chan256_supported(acf_in_dtype dt, int C, int P, long t_stride)
 {
@@ -269,8 +331,11 @@ bool chan256_supported(acf_in_dtype dt, int C, int P, long t_stride)
 
 cudaError_t launch_chan256(const void *hist, long n_hist, const void *samples, long n_samples, acf_in_dtype dt,
                            int n_sb, int N, const float *h, const float *bp, const float2 *tw, int out_kind,
-                           void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
+                           void *out, void *out_lo, long t_stride, float scale, long T, cudaStream_t s,
+                           void *scratch, size_t scratch_bytes)
 {
+    // the corner-turned path when the caller lends a buffer large enough
+    if (scratch && scratch_bytes < chan256_scratch_bytes(dt, n_sb, N, n_hist, n_samples)) scratch = nullptr;
     const long T64 = round_up(T, 64);
     if (T64 == 0) return cudaSuccess;
     if (N < 1 || n_sb < 1 || n_sb > 65535) return cudaErrorInvalidValue;
@@ -285,8 +350,8 @@ cudaError_t launch_chan256(const void *hist, long n_hist, const void *samples, l
     if (segs > 65535) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)N, (unsigned)segs, (unsigned)n_sb);
     switch (dt) {
-    case ACF_IN_CI8: return launch_dt<char2>(out_kind, hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, s);
-    case ACF_IN_CI16: return launch_dt<short2>(out_kind, hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, s);
+    case ACF_IN_CI8: return launch_dt<char2>(out_kind, hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, scratch, s);
+    case ACF_IN_CI16: return launch_dt<short2>(out_kind, hist, n_hist, samples, n_samples, n_sb, N, h, bp, tw, out, out_lo, t_stride, scale, T, mpb, grid, scratch, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -442,7 +442,8 @@ cudaError_t make_twiddles(int C, float2 **d_tw)
 cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples, long n_samples,
                               acf_in_dtype dt, int n_sb, int N, int C, int P, const float *h,
                               const float *bandpass, const float2 *tw, int out_kind, void *out,
-                              void *out_lo, long t_stride, float scale, long T, cudaStream_t s)
+                              void *out_lo, long t_stride, float scale, long T, cudaStream_t s, void *scratch,
+                              size_t scratch_bytes)
 {
     if (chan_ws_supported(dt, C, P, N, samples, n_samples)) {
         // spectra whose windows reach into the history: generic kernel; the
@@ -458,7 +459,7 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
     }
     if (chan256_supported(dt, C, P, t_stride))
         return launch_chan256(hist, n_hist, samples, n_samples, dt, n_sb, N, h, bandpass, tw, out_kind, out, out_lo,
-                              t_stride, scale, T, s);
+                              t_stride, scale, T, s, scratch, scratch_bytes);
     if (chan_fast_supported(dt, C, P))
         return launch_chan_fast(hist, n_hist, samples, n_samples, dt, n_sb, N, C, h, bandpass, tw, out_kind, out,
                                 out_lo, t_stride, scale, T, s);

@@ -57,6 +57,8 @@ struct acf_ctx {
     float *d_h = nullptr, *d_bp = nullptr;
     float2 *d_tw = nullptr;
     void *d_hist[2] = {nullptr, nullptr};
+    void *d_cturn = nullptr;      // 256-channel corner-turn scratch (optional)
+    size_t cturn_bytes = 0;
     int hist_cur = 0;
     long H = 0;                   // samples of history per subband
     void *d_X = nullptr, *d_Xlo = nullptr;
@@ -407,6 +409,17 @@ acf_status acf_create(acf_ctx **out, int n_inputs, int n_subbands, int n_channel
         acf_destroy(c);
         return st;
     }
+    if (chan256_supported(dtype, n_channels, n_taps, c->t_stride)) {
+        // input-major copy of history + push for the 256-channel kernel; when
+        // it cannot be had the kernel reads the [time][input] stream directly
+        const size_t cb = chan256_scratch_bytes(dtype, n_subbands, n_inputs, L, max_samples);
+        if (cudaMalloc(&c->d_cturn, cb) == cudaSuccess) {
+            c->cturn_bytes = cb;
+        } else {
+            cudaGetLastError();
+            c->d_cturn = nullptr;
+        }
+    }
     if (n_channels > 1 && (e = make_twiddles(n_channels, &c->d_tw)) != cudaSuccess) {
         acf_destroy(c);
         return cuda_fail(nullptr, e, "twiddles");
@@ -506,10 +519,13 @@ static acf_status push_common(acf_ctx *c, const void *dev_samples, long S, cudaS
             const char *hs = static_cast<const char *>(hist) + (size_t)sb * Hn * c->N * elem;
             char *hd = static_cast<char *>(next) + (size_t)sb * newH * c->N * elem;
             if (T > 0) {
+                // the scratch holds all subbands; a per-subband call uses its share
+                const size_t cshare = c->cturn_bytes / c->n_sb;
                 e = launch_channelise(Hn ? hs : nullptr, Hn, src, S, c->dt, nsb, c->N, c->C, c->P, c->d_h, c->d_bp,
                                       c->d_tw, out_kind, static_cast<char *>(c->d_X) + sb * x_sb,
                                       c->d_Xlo ? static_cast<char *>(c->d_Xlo) + sb * x_sb : nullptr, c->t_stride,
-                                      scale, T, s);
+                                      scale, T, s, c->d_cturn ? static_cast<char *>(c->d_cturn) + sb * cshare : nullptr,
+                                      (size_t)nsb * cshare);
                 if (e != cudaSuccess) return cuda_fail(c, e, "channelise");
             }
             e = launch_history(Hn ? hs : nullptr, Hn, src, S, c->dt, nsb, c->N, T * c->C, newH, hd, newH, s);
@@ -719,6 +735,7 @@ acf_status acf_destroy(acf_ctx *c)
     cudaFree(c->d_tw);
     cudaFree(c->d_hist[0]);
     cudaFree(c->d_hist[1]);
+    cudaFree(c->d_cturn);
     cudaFree(c->d_X);
     cudaFree(c->d_Xlo);
     cudaFree(c->d_V);
