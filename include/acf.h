@@ -131,6 +131,14 @@ acf_status acf_get_visibilities(acf_ctx *ctx, void *out, int *n_ready, acf_strea
  * integration is complete. */
 acf_status acf_visibilities_device(acf_ctx *ctx, const void **dev_ptr);
 
+/* Zero-copy alternative to acf_get_visibilities: finishes the completed
+ * integration in place (on `stream`) and re-arms the context without
+ * copying it.  The visibilities stay in the accumulator (acf_visibilities_device)
+ * until the next push's X-engine overwrites them; work that reads them must
+ * be ordered before that push (the same stream, or an event).  *n_ready as
+ * for acf_get_visibilities. */
+acf_status acf_release_visibilities(acf_ctx *ctx, int *n_ready, acf_stream_t stream);
+
 /* Spectra produced by the most recent push (per channel), the padded time
  * stride of the channelised operand, and the scale in use. */
 acf_status acf_query(acf_ctx *ctx, long *last_spectra, long *t_stride, float *scale);

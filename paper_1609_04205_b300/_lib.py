@@ -30,6 +30,7 @@ EXPORTS = [
     "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc", "acf_set_xengine_variant",
     "acf_delay_compensate", "acf_set_delays", "acf_integrate_channels", "acf_sigma_clip",
     "acf_lost_sample_weights", "acf_reweight", "acf_tune", "acf_query_xengine", "acf_probe_tensor_peak",
+    "acf_release_visibilities",
 ]
 
 
@@ -96,6 +97,7 @@ def lib():
         "acf_gain_forward_noalloc": ([P, P, P, I, I, P, P, P], I),
         "acf_set_xengine_variant": ([P, I], I),
         "acf_tune": ([P], I),
+        "acf_release_visibilities": ([P, ctypes.POINTER(I), P], I),
         "acf_probe_tensor_peak": ([Lg, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(F)], I),
         "acf_query_xengine": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "acf_delay_compensate": ([P, I, I, I, P, P, ctypes.c_double, P], I),

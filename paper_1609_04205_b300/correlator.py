@@ -122,6 +122,25 @@ class Correlator:
             return None
         return torch.view_as_complex(out) if out.dtype == torch.float32 else out
 
+    def release(self, stream=None) -> bool:
+        """Finish the completed integration in place without copying it
+        (acf_release_visibilities); True when one was complete.  Read it with
+        device_visibilities() before the next push (in stream order)."""
+        n = ctypes.c_int(0)
+        A.check(self._L.acf_release_visibilities(self._h, ctypes.byref(n), A.stream_handle(stream)), self._h)
+        return n.value == 1
+
+    def device_visibilities(self) -> torch.Tensor:
+        """Zero-copy view of the accumulator (acf_visibilities_device): complex64
+        [subbands][channels][baselines], or int64 [..][2] in INT8 mode."""
+        p = ctypes.c_void_p()
+        A.check(self._L.acf_visibilities_device(self._h, ctypes.byref(p)), self._h)
+        nb = self.n_inputs * (self.n_inputs + 1) // 2
+        int8 = self.mode == "int8"
+        view = _DeviceArray(p.value, (self.n_subbands, self.n_channels, nb, 2), "<i8" if int8 else "<f4")
+        t = torch.as_tensor(view, device="cuda")
+        return t if int8 else torch.view_as_complex(t)
+
     def enable_timing(self, on=True):
         A.check(self._L.acf_enable_timing(self._h, 1 if on else 0), self._h)
 
@@ -240,6 +259,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ over a device pointer the library owns (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = dict(shape=tuple(shape), typestr=typestr, data=(int(ptr), False),
+                                             version=3, strides=None)
 
 
 def launch_count() -> int:

@@ -619,10 +619,10 @@ acf_status acf_push_block_host(acf_ctx *c, const void *samples, long n_samples, 
     return push_common(c, c->d_stage, n_samples, s, &c->ev_copied);
 }
 
-acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_t stream)
+// Hand out a completed integration: finish it in place (the FP32 path's
+// delay rotation), copy it to `out` when given, and re-arm the context.
+static acf_status finish_integration(acf_ctx *c, void *out, int *n_ready, cudaStream_t s)
 {
-    if (!c) return ACF_EINVAL;
-    if (!out || !n_ready) return fail(c, ACF_EINVAL, "out / n_ready is NULL");
     *n_ready = 0;
     if (!c->ready) return ACF_OK;
     cudaError_t e = cudaSuccess;
@@ -630,16 +630,31 @@ acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_
         // the fp32 CUDA-core path has no fused rotation: the accumulator is
         // reset when the next integration starts, so rotate it in place (the
         // tensor-core X-engine applies the table in its flush)
-        e = launch_delay_apply(static_cast<float2 *>(c->d_V), c->d_delay_tab, (long)c->n_sb * c->C, c->N,
-                               (cudaStream_t)stream);
+        e = launch_delay_apply(static_cast<float2 *>(c->d_V), c->d_delay_tab, (long)c->n_sb * c->C, c->N, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "delay compensation");
     }
-    e = cudaMemcpyAsync(out, c->d_V, c->v_bytes, cudaMemcpyDefault, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy visibilities");
+    if (out) {
+        e = cudaMemcpyAsync(out, c->d_V, c->v_bytes, cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy visibilities");
+    }
     *n_ready = 1;
     c->ready = false;
     c->v_valid = false;
     return ACF_OK;
+}
+
+acf_status acf_get_visibilities(acf_ctx *c, void *out, int *n_ready, acf_stream_t stream)
+{
+    if (!c) return ACF_EINVAL;
+    if (!out || !n_ready) return fail(c, ACF_EINVAL, "out / n_ready is NULL");
+    return finish_integration(c, out, n_ready, (cudaStream_t)stream);
+}
+
+acf_status acf_release_visibilities(acf_ctx *c, int *n_ready, acf_stream_t stream)
+{
+    if (!c) return ACF_EINVAL;
+    if (!n_ready) return fail(c, ACF_EINVAL, "n_ready is NULL");
+    return finish_integration(c, nullptr, n_ready, (cudaStream_t)stream);
 }
 
 acf_status acf_set_delays(acf_ctx *c, const double *delays, const double *f_centre, double sample_rate)
