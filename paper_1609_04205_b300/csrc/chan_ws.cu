@@ -35,6 +35,7 @@
 #include <cstring>
 
 #include "acf_internal.h"
+#include "tc_ptx.cuh"
 
 namespace acf {
 namespace {
@@ -486,6 +487,387 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_ppf64_ws(const __grid_constan
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core variant for fp16 output.  The 64-point DFT of one (input,
+// spectrum) is a product with the 64 x 64 complex DFT matrix.  In real form a
+// batch (eight inputs x 16 spectra) is one tcgen05.mma of M = 128, N = 128,
+// K = 128 (eight K = 16 steps), fp16 operands, fp32 accumulation in TMEM:
+//     D[r][2c + o] = sum_k Y[r][k] W[2c + o][k],
+// Y row r = one (input, spectrum) of FIR outputs, column k = 2n + [imag part];
+// W row 2c + o = channel c's real (o = 0) or imaginary (o = 1) part.  With
+// W_64^(nc) = wr + i wi: Re z = sum wr yr - wi yi, Im z = sum wi yr + wr yi.
+// The bandpass weight times the output scale is applied in fp32 by the
+// epilogue, before the fp16 rounding.  The epilogue reads TMEM in the
+// 16-lane x 256-bit shape, which hands each thread two lanes eight apart;
+// the Y row map puts spectra mm and mm + 1 of one input there, so a thread
+// packs a time-contiguous pair of one output row directly, and each warp
+// store writes four whole 32-byte runs of output rows (the transpose of
+// Sec. 4.2.4).  Four accumulators (all 512 TMEM columns) let the epilogue
+// drain the batches of one 64-spectrum window together: the four 32-byte
+// pieces of an output row's 128-byte line leave in consecutive stores, which
+// DRAM takes at 5.4 TB/s against 3.5 TB/s for pieces a batch apart.
+// The FIR is written in transposed form: every new sample of a phase adds its
+// 16 tap products into a ring of 16 open spectra (independent FMAs), and the
+// spectrum that received its last tap leaves the ring.  Each spectrum still
+// sums h[0] x[s] + h[1] x[s+1] + ... in tap order, so its value equals the
+// direct form's.
+// Roles: warp 0 lane 0 TMA producer (input ring as in k_ppf64_ws, items of
+// eight inputs), warp 1 TMEM owner and MMA issuer, warps 2-5 epilogue (TMEM
+// lane quadrant = warp % 4), warps 6-13 FIR (thread = phase n, input pair).
+constexpr int kTcNI = 8;                 // inputs per item
+constexpr int kTcThreads = 448;
+constexpr int kTcFir0 = 6;               // first FIR warp
+constexpr int kTcEpiThreads = 128;
+constexpr uint32_t kTcCols = 512;        // four 128-column fp32 accumulators
+constexpr int kTcAcc = 4;
+constexpr uint32_t kTcIdesc = tc::idesc_f16_kmajor(128, 128);
+
+template <typename IN>
+struct TcGeo {
+    static constexpr int E = sizeof(IN);
+    static constexpr int ROWB = kTcNI * E;                 // stage row: 32 B (ci16) or 16 B (ci8)
+    static constexpr int STAGE = kRowsPerStage * ROWB;
+    static constexpr int STAGES = 4;
+    static constexpr int OFF_W = 0;                        // DFT matrix, 2 x [128 rows][128 B] SW128
+    static constexpr int OFF_Y = 32768;                    // FIR-output operands, two of 32 KB
+    static constexpr int OFF_X = OFF_Y + 65536;            // input ring
+    static constexpr int OFF_BAR = OFF_X + STAGES * STAGE;
+    static constexpr int NBAR = 2 * STAGES + 4 + 2 * kTcAcc + 1;
+    static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 1024;   // + alignment slack
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ void unpack_pair(const unsigned char *p, float2 (&x)[2], short2) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    x[0] = make_float2((float)(short)(w.x & 0xffffu), (float)(short)(w.x >> 16));
+    x[1] = make_float2((float)(short)(w.y & 0xffffu), (float)(short)(w.y >> 16));
+}
+__device__ __forceinline__ void unpack_pair(const unsigned char *p, float2 (&x)[2], char2) {
+    unpack<char2, 2>(lds32(p), x);
+}
+
+// Y row of input 2 ip + u, batch spectrum mm:
+//     r = 32 ip + 16 u + 8 (mm & 1) + ((mm >> 1) ^ 2 ip).
+// TMEM lanes 32 ip + 16 u .. + 15 hold input 2 ip + u; spectra 2x and 2x + 1
+// sit in lanes x ^ 2 ip and x ^ 2 ip + 8 of that group.  The rows one FIR
+// store instruction writes (four ip, fixed mm and u) differ in (r & 7) >> 1,
+// so under the 128-byte swizzle their 32-byte pieces use distinct banks.
+// yx[x]: this thread's byte offset in Y for mm >> 1 = x (K atom, row part
+// 32 ip + (x ^ 2 ip), swizzled chunk, position in the chunk); 128 (16u + 8
+// (mm & 1)) is added per store.
+template <typename IN, bool MASK>
+__device__ __forceinline__ void fir_batch_tc(const float2 (&hr)[kP], float2 (&acc)[2][kP], const unsigned char *xs,
+                                             unsigned char *yb, int xoff, const int (&yx)[8], long m0, long T)
+{
+    using G = TcGeo<IN>;
+    // samples are read and widened two steps ahead of their FMAs
+    float2 xa[2], xb[2];
+    unpack_pair(xs + xoff, xa, IN{});
+    unpack_pair(xs + kC * G::ROWB + xoff, xb, IN{});
+#pragma unroll
+    for (int mm = 0; mm < kMB; ++mm) {
+        const float2 xv[2] = {xa[0], xa[1]};
+        xa[0] = xb[0];
+        xa[1] = xb[1];
+        if (mm + 2 < kMB) unpack_pair(xs + (mm + 2) * kC * G::ROWB + xoff, xb, IN{});
+        // this sample is tap k of spectrum m0 + mm + 15 - k, whose ring slot is (mm + 15 - k) & 15
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            acc[u][(mm + 15) & 15] = __fmul2_rn(hr[0], xv[u]);
+#pragma unroll
+            for (int k = 1; k < kP; ++k) acc[u][(mm + 15 - k) & 15] = __ffma2_rn(hr[k], xv[u], acc[u][(mm + 15 - k) & 15]);
+        }
+        // spectrum m0 + mm received its last tap
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float2 y = acc[u][mm & 15];
+            if (MASK && m0 + mm >= T) y = make_float2(0.f, 0.f);
+            *reinterpret_cast<__half2 *>(yb + 128 * (16 * u + 8 * (mm & 1)) + yx[mm >> 1]) = __floats2half2_rn(y.x, y.y);
+        }
+    }
+}
+
+// Drain NB consecutive batches (accumulators g .. g + NB - 1, mod 4) of one
+// epilogue thread: for each input half u and each pair of its channels, load
+// the NB batches' values, scale by the channel's weight, round to fp16 and
+// store the (mm, mm + 1) pairs of the real and imaginary rows; the NB stores
+// of one row go out back to back (16 NB spectra of the row).  o: real row of
+// (channel t4, input 2q) at the window's first spectrum + mm.
+template <int NB>
+__device__ __forceinline__ void epi_window(uint32_t taddr, long g, __half *o, long cstride, long ts, const float2 *gs,
+                                           int t4)
+{
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll 2
+        for (int j8 = 0; j8 < 8; ++j8) {
+            uint32_t r[NB][8];
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                tc::tmem_ld16x256_x2(taddr + ((uint32_t)(16 * u) << 16) + (uint32_t)(((g + k) & (kTcAcc - 1)) * 128) + 16 * j8,
+                                     r[k]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int c = t4 + 4 * (2 * j8 + jj);
+                const float2 gc = gs[c];
+                __half *orow = o + (long)(c - t4) * cstride + 2L * u * ts;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const float2 re = __fmul2_rn(make_float2(__uint_as_float(r[k][4 * jj]), __uint_as_float(r[k][4 * jj + 2])), gc);
+                    *reinterpret_cast<__half2 *>(orow + kMB * k) = __floats2half2_rn(re.x, re.y);
+                }
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const float2 im = __fmul2_rn(make_float2(__uint_as_float(r[k][4 * jj + 1]), __uint_as_float(r[k][4 * jj + 3])), gc);
+                    *reinterpret_cast<__half2 *>(orow + ts + kMB * k) = __floats2half2_rn(im.x, im.y);
+                }
+            }
+        }
+    }
+}
+
+template <typename IN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constant__ WsParams P)
+{
+    using G = TcGeo<IN>;
+    constexpr int NS = G::STAGES;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ int abort_flag;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float2 tw[kC];     // W_64^t = cos - i sin: (cos, sin)
+    __shared__ float2 gs[kC];     // bandpass x output scale, both halves
+    const uint32_t s0 = su32(smem);
+    const uint32_t bar0 = s0 + G::OFF_BAR;
+    auto xfull = [&](int s) { return bar0 + 8u * s; };
+    auto xempty = [&](int s) { return bar0 + 8u * (NS + s); };
+    auto yfull = [&](int b) { return bar0 + 8u * (2 * NS + b); };
+    auto yempty = [&](int b) { return bar0 + 8u * (2 * NS + 2 + b); };
+    auto dfull = [&](int b) { return bar0 + 8u * (2 * NS + 4 + b); };
+    auto dempty = [&](int b) { return bar0 + 8u * (2 * NS + 4 + kTcAcc + b); };
+    const uint32_t done = bar0 + 8u * (2 * NS + 4 + 2 * kTcAcc);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NS; ++s) {
+            bar_init(xfull(s), 1);
+            bar_init(xempty(s), kFirThreads);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(yfull(b), kFirThreads);
+            bar_init(yempty(b), 1);
+        }
+        for (int b = 0; b < kTcAcc; ++b) {
+            bar_init(dfull(b), 1);
+            bar_init(dempty(b), kTcEpiThreads);
+        }
+        bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.map)) : "memory");
+    }
+    if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_slot), kTcCols);
+    if (tid < kC) {
+        double sn, cs;
+        sincospi((double)tid / 32.0, &sn, &cs);
+        tw[tid] = make_float2((float)cs, (float)sn);
+        const float g = __ldg(P.bp + tid) * P.osc;
+        gs[tid] = make_float2(g, g);
+    }
+    __syncthreads();
+    // W row l = 2c + o, column pair (2n, 2n + 1): o = 0 (wr, -wi) = (cos, sin), o = 1 (wi, wr) = (-sin, cos)
+    for (int e = tid; e < 128 * kC; e += kTcThreads) {
+        const int l = e >> 6, n = e & 63, c = l >> 1;
+        const float2 t = tw[(n * c) & 63];
+        const __half2 v = (l & 1) == 0 ? __floats2half2_rn(t.x, t.y) : __floats2half2_rn(-t.y, t.x);
+        const int off = (n >> 5) * 16384 + l * 128 + ((((n & 31) >> 2) ^ (l & 7)) << 4) + 4 * (n & 3);
+        *reinterpret_cast<__half2 *>(smem + G::OFF_W + off) = v;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            long issued = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                const ItemPos d = decode_item(P, item);
+                const long nb = (d.m_hi - d.m_lo) / kMB;
+                for (long j = 0; j <= nb && ok; ++j) {
+                    const int s = (int)(issued % NS);
+                    if (issued >= NS &&
+                        !bar_wait(xempty(s), (uint32_t)(((issued / NS) - 1) & 1), &abort_flag, P.err, 31)) {
+                        ok = false;
+                        break;
+                    }
+                    const long srow = j == 0 ? d.m_lo * kC : (d.m_lo + kMB * (j - 1) + (kP - 1)) * kC;
+                    const long y = srow + P.row0;
+                    bar_expect(xfull(s), G::STAGE);
+#pragma unroll
+                    for (int q = 0; q < kRowsPerStage / kBoxRows; ++q)
+                        tma_3d(s0 + G::OFF_X + s * G::STAGE + q * kBoxRows * G::ROWB, &P.map, xfull(s), d.grp * kTcNI,
+                               (int)(y + q * kBoxRows), d.sb);
+                    ++issued;
+                }
+            }
+            // let the copies in flight land (all were consumed unless the CTA aborted)
+            for (long q = issued - 1; q >= 0 && q >= issued - NS; --q) {
+                const int s = (int)(q % NS);
+                for (long long it = 0; it < (1LL << 22) && !bar_test(xfull(s), (uint32_t)((q / NS) & 1)); ++it)
+                    __nanosleep(256);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            long g = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+                const ItemPos d = decode_item(P, item);
+                for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++g) {
+                    const int b = (int)(g & 1), da = (int)(g & (kTcAcc - 1));
+                    ok = bar_wait(yfull(b), (uint32_t)((g >> 1) & 1), &abort_flag, P.err, 32);
+                    if (ok && g >= kTcAcc)
+                        ok = bar_wait(dempty(da), (uint32_t)(((g / kTcAcc) - 1) & 1), &abort_flag, P.err, 33);
+                    if (!ok) break;
+                    tc::fence_after();
+                    const uint32_t ya = s0 + G::OFF_Y + b * 32768;
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const uint32_t koff = (ks >> 2) * 16384 + (ks & 3) * 32;
+                        tc::mma_f16(tmem + da * 128, tc::desc_kmajor_sw128(ya + koff),
+                                    tc::desc_kmajor_sw128(s0 + G::OFF_W + koff), kTcIdesc, ks > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(yempty(b));
+                    tc::mma_commit(dfull(da));
+                }
+            }
+            // every MMA issued completes before TMEM is released
+            tc::mma_commit(done);
+            for (long long it = 0; it < (1LL << 22) && !bar_test(done, 0); ++it) __nanosleep(256);
+        }
+    } else if (warp < kTcFir0) {
+        // ---------------- epilogue ----------------
+        // warp quadrant q holds inputs 2q (lanes 32q .. + 15) and 2q + 1; in a
+        // 16-lane group thread t reads lanes t / 4 and t / 4 + 8, i.e.
+        // spectra mm = 2 ((t / 4) ^ 2q) and mm + 1, and channels t % 4 + 4k.
+        // The batches of one 64-spectrum window (1 to 4 of them) are drained
+        // together.
+        const int q = warp & 3, t4 = lane & 3;
+        const int mm = 2 * ((lane >> 2) ^ (2 * q));
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+        const long cstride = 2L * P.N * P.t_stride;           // elements between channels
+        __half *out = static_cast<__half *>(P.out);
+        long g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const ItemPos d = decode_item(P, item);
+            // real row of (channel t4, input 2q), time mm
+            __half *ob = out + ((long)d.sb * kC * 2 * P.N + 2L * (d.grp * kTcNI + 2 * q)) * P.t_stride + t4 * cstride + mm;
+            for (long m0 = d.m_lo; m0 < d.m_hi && ok;) {
+                const long wend = min(d.m_hi, (m0 / (kTcAcc * kMB) + 1) * (kTcAcc * kMB));
+                const int nbw = (int)((wend - m0) / kMB);
+                for (int k = 0; k < nbw && ok; ++k)
+                    ok = bar_wait(dfull((int)((g + k) & (kTcAcc - 1))), (uint32_t)(((g + k) / kTcAcc) & 1), &abort_flag,
+                                  P.err, 34);
+                if (!ok) break;
+                tc::fence_after();
+                switch (nbw) {
+                case 1: epi_window<1>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
+                case 2: epi_window<2>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
+                case 3: epi_window<3>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
+                default: epi_window<4>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
+                }
+                tc::fence_before();
+                for (int k = 0; k < nbw; ++k) bar_arrive(dempty((int)((g + k) & (kTcAcc - 1))));
+                g += nbw;
+                m0 = wend;
+            }
+        }
+    } else {
+        // ---------------- FIR warps ----------------
+        const int fi = tid - 32 * kTcFir0, ip = fi & 3, n = fi >> 2;
+        float2 hr[kP];
+#pragma unroll
+        for (int k = 0; k < kP; ++k) {
+            const float hv = __ldg(P.h + k * kC + n);
+            hr[k] = make_float2(hv, hv);
+        }
+        float2 acc[2][kP];
+        const int xoff = n * G::ROWB + ip * 2 * G::E;
+        const int ch = (n & 31) >> 2, kb = (n >> 5) * 16384 + 32 * ip * 128 + 4 * (n & 3);
+        int yx[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int xr = x ^ (2 * ip);
+            yx[x] = kb + xr * 128 + ((ch ^ xr) << 4);
+        }
+        long L = 0, g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
+            const ItemPos d = decode_item(P, item);
+            // prologue: the first 15 rows of the item's first window; sample k
+            // is tap k - s of spectrum m_lo + s, s = 0 .. k
+            ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 35);
+            if (!ok) break;
+            {
+                const unsigned char *xs = smem + G::OFF_X + (L % NS) * G::STAGE;
+#pragma unroll
+                for (int k = 0; k < kP - 1; ++k) {
+                    float2 xv[2];
+                    unpack_pair(xs + k * kC * G::ROWB + xoff, xv, IN{});
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        acc[u][k] = __fmul2_rn(hr[0], xv[u]);
+#pragma unroll
+                        for (int s = 0; s < k; ++s) acc[u][s] = __ffma2_rn(hr[k - s], xv[u], acc[u][s]);
+                    }
+                }
+                bar_arrive(xempty((int)(L % NS)));
+                ++L;
+            }
+            for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++g) {
+                const int b = (int)(g & 1);
+                if (g >= 2) ok = bar_wait(yempty(b), (uint32_t)(((g >> 1) - 1) & 1), &abort_flag, P.err, 36);
+                if (ok) ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 37);
+                if (!ok) break;
+                const unsigned char *xs = smem + G::OFF_X + (L % NS) * G::STAGE;
+                unsigned char *yb = smem + G::OFF_Y + b * 32768;
+                if (m0 + kMB <= P.T) fir_batch_tc<IN, false>(hr, acc, xs, yb, xoff, yx, m0, P.T);
+                else fir_batch_tc<IN, true>(hr, acc, xs, yb, xoff, yx, m0, P.T);
+                tc::fence_proxy_async();
+                bar_arrive(xempty((int)(L % NS)));
+                bar_arrive(yfull(b));
+                ++L;
+            }
+        }
+    }
+
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTcCols);
+    }
+}
+
+template <typename IN>
+cudaError_t launch_tc_t(WsParams &P, int grid, cudaStream_t s)
+{
+    using G = TcGeo<IN>;
+    auto kern = k_ppf64_tc<IN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kTcThreads, G::SMEM, s>>>(P);
+    g_launches++;
+    return cudaGetLastError();
+}
+
 template <typename IN, int OUTK>
 cudaError_t launch_ws_t(WsParams &P, int grid, cudaStream_t s)
 {
@@ -521,11 +903,15 @@ cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf
     const long m_begin = chan_ws_first_spectrum(n_hist);
     const long m_end = round_up(T, 64);
     if (m_end <= m_begin) return cudaSuccess;
-    const int E = in_elem_bytes(dt), NI = 16 / E;
+    const int E = in_elem_bytes(dt);
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!enc) return cudaErrorNotSupported;
     WsParams P;
     std::memset(&P, 0, sizeof(P));
+    // fp16 output takes the tensor-core DFT (items of eight inputs)
+    const bool use_tc = out_kind == OUT_F16 && N % kTcNI == 0 && t_stride % 2 == 0 &&
+                        reinterpret_cast<uintptr_t>(out) % 4 == 0;
+    const int NI = use_tc ? kTcNI : 16 / E;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)n_samples, (cuuint64_t)n_sb};
     cuuint64_t strides[2] = {(cuuint64_t)N * E, (cuuint64_t)n_samples * N * E};
     cuuint32_t box[3] = {(cuuint32_t)NI, (cuuint32_t)kBoxRows, 1};
@@ -574,6 +960,7 @@ cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf
     if (items > 0x7fffffffL) return cudaErrorInvalidValue;
     P.n_items = (int)items;
     const int grid = (int)std::min<long>(items, sms);
+    if (use_tc) return dt == ACF_IN_CI16 ? launch_tc_t<short2>(P, grid, s) : launch_tc_t<char2>(P, grid, s);
     if (dt == ACF_IN_CI16) {
         switch (out_kind) {
         case OUT_F32: return launch_ws_t<short2, OUT_F32>(P, grid, s);
