@@ -203,8 +203,15 @@ def time_mode(acf, torch, x, w, mode, steps, warmup, stream, flush=None, keep=No
     S = w["n_samples"]
     c = acf.Correlator(N, n_sb, C, P, 1, mode, w["dtype"], S)
     # the context's autotuner picks the X-engine launch shape on this geometry
-    # (untimed, before the warm-up); the FP32 comparison path has none
-    tuning = c.tune() if mode != "fp32" else None
+    # (untimed), on the operands of one warm-up integration of the live
+    # samples; the FP32 comparison path has none
+    tuning = None
+    if mode != "fp32":
+        with torch.cuda.stream(stream):
+            c.push(x, stream)
+            c.release(stream)
+        stream.synchronize()
+        tuning = c.tune()
     c.enable_timing(True)
     Ts, chan_ms, xeng_ms = [], [], []
     with torch.cuda.stream(stream):
@@ -458,9 +465,11 @@ def profile_case(mode):
     sky = synth.make_sky(w["n_inputs"], w["n_sources"], w["flux"], w["seed"]) if w["n_sources"] else None
     x = synth.voltages(w["n_inputs"], w["n_samples"], 1, w["dtype"], w["sigma"], sky, w["seed"], device="cuda")
     with acf.Correlator(w["n_inputs"], 1, w["n_channels"], w["n_taps"], 1, mode, w["dtype"], w["n_samples"]) as c:
-        if mode != "fp32":
-            c.tune()
         out = c.empty_visibilities()
+        if mode != "fp32":
+            c.push(x)                  # tune on one integration of the live samples
+            c.visibilities(out)
+            c.tune()
         for _ in range(4):
             c.push(x)
             c.visibilities(out)
@@ -607,9 +616,12 @@ def main():
         try:
             xh = x.cpu().pin_memory()
             c = acf.Correlator(N, n_sb, w["n_channels"], w["n_taps"], 1, "fp16", w["dtype"], S)
-            c.tune()
             outh = torch.empty((n_sb, w["n_channels"], N * (N + 1) // 2, 2), dtype=torch.float32).pin_memory()
             with torch.cuda.stream(stream):
+                c.push(xh, stream)               # tune on one integration of the live samples
+                c.visibilities(outh, stream)
+                stream.synchronize()
+                c.tune()
                 for _ in range(2):
                     c.push(xh, stream)
                     c.visibilities(outh, stream)

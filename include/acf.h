@@ -165,7 +165,11 @@ acf_status acf_set_xengine_variant(acf_ctx *ctx, int variant);
  * split 1, 2 or 4) on the context's full launch (its first subband's
  * problems when the scratch for all of them cannot be had), writing a
  * temporary visibility buffer (allocated and freed here), and rebuilds the
- * launch plan with the fastest.  Only between integrations (ESTATE
+ * launch plan with the fastest.  The candidates run on the operand buffer as
+ * it stands: zeros before the first push, the last push's operands after an
+ * integration.  Tensor-core power, and so the clock under the power cap,
+ * depends on the data, so tuning after one integration of live samples ranks
+ * the shapes as the pushes will run them.  Only between integrations (ESTATE
  * otherwise, and in FP32 mode); ENOMEM when the scratch cannot be had.
  * Synchronises the device. */
 acf_status acf_tune(acf_ctx *ctx);
