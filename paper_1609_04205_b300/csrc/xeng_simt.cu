@@ -4,12 +4,17 @@
 // of 32x32 receivers, one work-group each, every thread holding a 2x2
 // receiver tile in registers across the time loop.  Here a 128-thread block
 // owns a 64x64 square of complex inputs and each thread an 8x4 tile (rows
-// ty + 8a, columns tx + 16b), so every operand value a thread loads from
-// shared memory feeds 4 (row) or 8 (column) complex multiply-accumulates.
-// Each complex MAC V_ij += x_i conj(y_j) is two packed fp32x2 FMAs on
-//   (re, im) += (xr, xi) * (yr, yr)   and   (re, im) += (xi, xr) * (yi, -yi),
-// so the shared stages hold the rows pre-arranged as (xr, xi, xi, xr) and the
-// columns as (yr, yr, yi, -yi): one 16-byte load per operand per MAC pair.
+// 2ty + 16a + {0, 1}, columns tx + 16b), so every operand value a thread
+// loads from shared memory feeds 4 (row) or 8 (column) complex MACs.  The
+// packed fp32x2 FMAs run over pairs of adjacent rows i0, i1: for V_ij +=
+// x_i conj(y_j),
+//   Re += (xr0, xr1) * (yr, yr) + (xi0, xi1) * (yi, yi)
+//   Im += (xi0, xi1) * (yr, yr) - (xr0, xr1) * (yi, yi),
+// so the row operand is read as (xr0, xr1) and (xi0, xi1) from separate real
+// and imaginary planes and only the column value is duplicated in registers.
+// The stages hold each operand value once (8 bytes a complex value): 3 bytes
+// of shared-memory reads per complex MAC, 96 of the SM's 128 B/clk at the
+// full FMA rate.
 // Stages of 16 spectra are double buffered: the next stage's global loads
 // (four lanes per 64-byte row piece) are in flight while the current one is
 // multiplied.  Partial sums are flushed to
@@ -25,7 +30,7 @@ constexpr int BT = 64;          // complex inputs per tile side
 constexpr int KT = 16;          // spectra per stage
 constexpr int NTH = 128;        // threads per block
 constexpr int CHUNK = 4096;     // spectra per partial sum
-constexpr size_t SMEM_SIMT = 2ull * 2 * KT * BT * sizeof(float4);   // A and B, two buffers: 64 KB
+constexpr size_t SMEM_SIMT = 2ull * 2 * KT * BT * sizeof(float2);   // A and B, two buffers: 32 KB
 
 __device__ __forceinline__ void tri_decode(int k, int &bi, int &bj) {
     int b = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
@@ -48,9 +53,10 @@ __device__ __forceinline__ float4 row4(const float *src, long t, long n_time) {
 __global__ void __launch_bounds__(NTH, 3)
 k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, float vscale, float2 *__restrict__ V)
 {
-    extern __shared__ __align__(16) float4 sm[];
-    float4 (*As)[KT][BT] = reinterpret_cast<float4 (*)[KT][BT]>(sm);                 // [buf][t][i]
-    float4 (*Bs)[KT][BT] = reinterpret_cast<float4 (*)[KT][BT]>(sm + 2 * KT * BT);  // [buf][t][j]
+    extern __shared__ __align__(16) float2 sm[];
+    float (*Ar)[KT][BT] = reinterpret_cast<float (*)[KT][BT]>(sm);                   // [buf][t][i], real parts
+    float (*Ai)[KT][BT] = reinterpret_cast<float (*)[KT][BT]>(sm + KT * BT);         // imaginary parts
+    float2 (*Bs)[KT][BT] = reinterpret_cast<float2 (*)[KT][BT]>(sm + 2 * KT * BT);  // [buf][t][j], (re, im)
     int bi, bj;
     tri_decode(blockIdx.x, bi, bj);
     const long p = blockIdx.y;
@@ -61,9 +67,11 @@ k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, floa
     // staging: threads 0-63 stage the A rows, 64-127 the B rows.  A thread
     // covers (4-spectrum group tg, input il) for il = il0 + 16 q: four lanes
     // read one row's 16 spectra (64 contiguous bytes), a warp 8 rows.  The
-    // stage column of (t, i) is i ^ sw(t), sw(t) = 2 * ((t >> 2) & 3), which
-    // keeps the transposing 16-byte stores of a quarter-warp (4 groups x 2
-    // inputs) on distinct banks; the MAC loads apply the same swizzle.
+    // stage column of (t, i) is i ^ sw(t): for the 4-byte planes of A
+    // sw(t) = 8 * ((t >> 2) & 3), for the 8-byte (re, im) values of B
+    // sw(t) = 4 * ((t >> 2) & 3); either keeps the transposing stores of a
+    // warp on distinct banks (and adjacent A rows adjacent); the MAC loads
+    // apply the same swizzles.
     const int se = tid & 63, tg = se & 3, il0 = se >> 2;
     const bool stage_b = tid >= 64;
     const int nbase = stage_b ? j0 : i0;
@@ -85,33 +93,44 @@ k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, floa
     auto deposit = [&](int buf) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int col = (il0 + 16 * q) ^ (2 * tg);
             const float r[4] = {pre[q][0].x, pre[q][0].y, pre[q][0].z, pre[q][0].w};
             const float m[4] = {pre[q][1].x, pre[q][1].y, pre[q][1].z, pre[q][1].w};
+            if (stage_b) {
+                const int col = (il0 + 16 * q) ^ (4 * tg);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (stage_b) Bs[buf][4 * tg + k][col] = make_float4(r[k], r[k], m[k], -m[k]);
-                else As[buf][4 * tg + k][col] = make_float4(r[k], m[k], m[k], r[k]);
+                for (int k = 0; k < 4; ++k) Bs[buf][4 * tg + k][col] = make_float2(r[k], m[k]);
+            } else {
+                const int col = (il0 + 16 * q) ^ (8 * tg);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    Ar[buf][4 * tg + k][col] = r[k];
+                    Ai[buf][4 * tg + k][col] = m[k];
+                }
             }
         }
     };
 
-    float2 acc[8][4];
+    // accR[a][b] = (Re V, Re V) and accI[a][b] = (Im V, Im V) of rows
+    // 2ty + 16a and 2ty + 16a + 1 against column tx + 16b
+    float2 accR[4][4], accI[4][4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < 4; ++b) accR[a][b] = accI[a][b] = make_float2(0.f, 0.f);
 
     const long NB = (long)N * (N + 1) / 2;
     auto flush = [&]() {
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int i = i0 + ty + 8 * a, j = j0 + tx + 16 * b;
+                const int i = i0 + 2 * ty + 16 * a, j = j0 + tx + 16 * b;
                 if (i < N && j <= i)
-                    atomicAdd(&V[p * NB + (long)i * (i + 1) / 2 + j], make_float2(acc[a][b].x * vscale, acc[a][b].y * vscale));
-                acc[a][b] = make_float2(0.f, 0.f);
+                    atomicAdd(&V[p * NB + (long)i * (i + 1) / 2 + j], make_float2(accR[a][b].x * vscale, accI[a][b].x * vscale));
+                if (i + 1 < N && j <= i + 1)
+                    atomicAdd(&V[p * NB + (long)(i + 1) * (i + 2) / 2 + j],
+                              make_float2(accR[a][b].y * vscale, accI[a][b].y * vscale));
+                accR[a][b] = accI[a][b] = make_float2(0.f, 0.f);
             }
     };
 
@@ -123,21 +142,28 @@ k_xeng_simt(const float *__restrict__ x, int N, long n_time, long t_stride, floa
     for (long t0 = 0; t0 < n_time; t0 += KT) {
         const bool more = t0 + KT < n_time;
         if (more) fetch(t0 + KT);            // in flight during this stage's MACs
-#pragma unroll 4
+#pragma unroll 2
         for (int tt = 0; tt < KT; ++tt) {
-            const int sw = 2 * ((tt >> 2) & 3);
-            float4 av[8], bv[4];
+            const int swa = 8 * ((tt >> 2) & 3), swb = 4 * ((tt >> 2) & 3);
+            float2 xr[4], xi[4], bv[4];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) av[a] = As[buf][tt][(ty + 8 * a) ^ sw];
+            for (int a = 0; a < 4; ++a) {
+                xr[a] = *reinterpret_cast<const float2 *>(&Ar[buf][tt][(2 * ty + 16 * a) ^ swa]);
+                xi[a] = *reinterpret_cast<const float2 *>(&Ai[buf][tt][(2 * ty + 16 * a) ^ swa]);
+            }
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][tt][(tx + 16 * b) ^ sw];
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][tt][(tx + 16 * b) ^ swb];
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const float2 yr = make_float2(bv[b].x, bv[b].x), yi = make_float2(bv[b].y, bv[b].y);
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b] = __ffma2_rn(make_float2(av[a].x, av[a].y), make_float2(bv[b].x, bv[b].y), acc[a][b]);
-                    acc[a][b] = __ffma2_rn(make_float2(av[a].z, av[a].w), make_float2(bv[b].z, bv[b].w), acc[a][b]);
+                for (int a = 0; a < 4; ++a) {
+                    accR[a][b] = __ffma2_rn(xr[a], yr, accR[a][b]);
+                    accR[a][b] = __ffma2_rn(xi[a], yi, accR[a][b]);
+                    accI[a][b] = __ffma2_rn(xi[a], yr, accI[a][b]);
+                    accI[a][b] = __ffma2_rn(make_float2(-xr[a].x, -xr[a].y), yi, accI[a][b]);
                 }
+            }
         }
         since += KT;
         if (since >= CHUNK && more) {
