@@ -446,15 +446,15 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
                               size_t scratch_bytes)
 {
     if (chan_ws_supported(dt, C, P, N, samples, n_samples)) {
-        // spectra whose windows reach into the history: generic kernel; the
-        // rest (all of them after the first 16 of a push): warp-specialised kernel
-        const long m_head = std::min(chan_ws_first_spectrum(n_hist), round_up(T, 64));
+        // spectra whose windows reach into the history and that the
+        // warp-specialised kernel does not read itself: generic kernel
+        const long m_head = std::min(chan_ws_begin(dt, out_kind, N, t_stride, out, hist, n_hist), round_up(T, 64));
         cudaError_t e = cudaSuccess;
         if (m_head > 0)
             e = launch_channelise_head(hist, n_hist, samples, n_samples, dt, n_sb, N, C, P, h, bandpass, tw, out_kind,
                                        out, out_lo, t_stride, scale, T, m_head, s);
         if (e != cudaSuccess) return e;
-        return launch_chan_ws(samples, n_samples, n_hist, dt, n_sb, N, h, bandpass, scale, out_kind, out, out_lo,
+        return launch_chan_ws(hist, samples, n_samples, n_hist, dt, n_sb, N, h, bandpass, scale, out_kind, out, out_lo,
                               t_stride, T, s);
     }
     if (chan256_supported(dt, C, P, t_stride))

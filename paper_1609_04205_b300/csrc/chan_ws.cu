@@ -88,6 +88,8 @@ struct WsParams {
     long seg;             // spectra per item, a multiple of 16
     int groups, n_sb, n_items, N;
     int *err;
+    const void *hist;     // tensor-core variant: [n_sb][n_hist][N] samples before the push (n_hist < 1024)
+    long n_hist;
 };
 
 // ---- small PTX helpers --------------------------------------------------------
@@ -555,14 +557,25 @@ __device__ __forceinline__ void unpack_pair(const unsigned char *p, float2 (&x)[
 // yx[x]: this thread's byte offset in Y for mm >> 1 = x (K atom, row part
 // 32 ip + (x ^ 2 ip), swizzled chunk, position in the chunk); 128 (16u + 8
 // (mm & 1)) is added per store.
+// This thread's input pair at one stream row of the history (global memory).
+__device__ __forceinline__ void hist_pair(const void *h, long e, float2 (&x)[2], short2) {
+    unpack_pair(static_cast<const unsigned char *>(h) + e * 4, x, short2{});
+}
+__device__ __forceinline__ void hist_pair(const void *h, long e, float2 (&x)[2], char2) {
+    unpack<char2, 2>(*reinterpret_cast<const uint32_t *>(static_cast<const unsigned char *>(h) + e * 2), x);
+}
+
+// h0 >= 0: the batch's first sample lies in the history, at element h0.
 template <typename IN, bool MASK>
 __device__ __forceinline__ void fir_batch_tc(const float2 (&hr)[kP], float2 (&acc)[2][kP], const unsigned char *xs,
-                                             unsigned char *yb, int xoff, const int (&yx)[8], long m0, long T)
+                                             unsigned char *yb, int xoff, const int (&yx)[8], long m0, long T,
+                                             const void *hist, long h0)
 {
     using G = TcGeo<IN>;
     // samples are read and widened two steps ahead of their FMAs
     float2 xa[2], xb[2];
-    unpack_pair(xs + xoff, xa, IN{});
+    if (h0 >= 0) hist_pair(hist, h0, xa, IN{});
+    else unpack_pair(xs + xoff, xa, IN{});
     unpack_pair(xs + kC * G::ROWB + xoff, xb, IN{});
 #pragma unroll
     for (int mm = 0; mm < kMB; ++mm) {
@@ -812,7 +825,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const ItemPos d = decode_item(P, item);
             // prologue: the first 15 rows of the item's first window; sample k
-            // is tap k - s of spectrum m_lo + s, s = 0 .. k
+            // is tap k - s of spectrum m_lo + s, s = 0 .. k.  An item that
+            // starts at spectrum 0 of a push with history reads the stream rows
+            // before the push from the history (the TMA stage holds zeros there).
+            const bool from_hist = d.m_lo == 0 && P.n_hist > 0;
+            const long hrow0 = ((long)d.sb * P.n_hist) * P.N + d.grp * kTcNI + 2 * ip;   // history element of row 0
             ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 35);
             if (!ok) break;
             {
@@ -820,7 +837,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
 #pragma unroll
                 for (int k = 0; k < kP - 1; ++k) {
                     float2 xv[2];
-                    unpack_pair(xs + k * kC * G::ROWB + xoff, xv, IN{});
+                    const long row = (long)k * kC + n;
+                    if (from_hist && row < P.n_hist) hist_pair(P.hist, hrow0 + row * P.N, xv, IN{});
+                    else unpack_pair(xs + k * kC * G::ROWB + xoff, xv, IN{});
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         acc[u][k] = __fmul2_rn(hr[0], xv[u]);
@@ -838,8 +857,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
                 if (!ok) break;
                 const unsigned char *xs = smem + G::OFF_X + (L % NS) * G::STAGE;
                 unsigned char *yb = smem + G::OFF_Y + b * 32768;
-                if (m0 + kMB <= P.T) fir_batch_tc<IN, false>(hr, acc, xs, yb, xoff, yx, m0, P.T);
-                else fir_batch_tc<IN, true>(hr, acc, xs, yb, xoff, yx, m0, P.T);
+                // the first batch's first sample is stream row 15 * 64 + n
+                const long r0 = (long)(kP - 1) * kC + n;
+                const long h0 = (from_hist && m0 == 0 && r0 < P.n_hist) ? hrow0 + r0 * P.N : -1;
+                if (m0 + kMB <= P.T) fir_batch_tc<IN, false>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
+                else fir_batch_tc<IN, true>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
                 tc::fence_proxy_async();
                 bar_arrive(xempty((int)(L % NS)));
                 bar_arrive(yfull(b));
@@ -890,17 +912,36 @@ bool chan_ws_supported(acf_in_dtype dt, int C, int P, int N, const void *samples
     return N % ni == 0 && reinterpret_cast<uintptr_t>(samples) % 16 == 0 && tensor_map_encoder() != nullptr;
 }
 
+// fp16 output takes the tensor-core DFT (items of eight inputs)
+static bool tc_variant(acf_in_dtype, int out_kind, int N, long t_stride, const void *out)
+{
+    return out_kind == OUT_F16 && N % kTcNI == 0 && t_stride % 2 == 0 && reinterpret_cast<uintptr_t>(out) % 4 == 0;
+}
+// ... which also covers the spectra whose windows reach into a history
+// shorter than one window (the streaming context's filter state)
+static bool tc_reads_history(acf_in_dtype dt, const void *hist, long n_hist)
+{
+    return hist && n_hist > 0 && n_hist < (long)kC * kP &&
+           reinterpret_cast<uintptr_t>(hist) % (dt == ACF_IN_CI16 ? 8 : 4) == 0;
+}
+
 long chan_ws_first_spectrum(long n_hist)
 {
     // first spectrum whose window starts inside the pushed samples, rounded up to a batch
     return round_up((n_hist + kC - 1) / kC, kMB);
 }
 
-cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf_in_dtype dt, int n_sb, int N,
-                           const float *h, const float *bp, float scale, int out_kind, void *out, void *out_lo,
-                           long t_stride, long T, cudaStream_t s)
+long chan_ws_begin(acf_in_dtype dt, int out_kind, int N, long t_stride, const void *out, const void *hist, long n_hist)
 {
-    const long m_begin = chan_ws_first_spectrum(n_hist);
+    if (tc_variant(dt, out_kind, N, t_stride, out) && (n_hist == 0 || tc_reads_history(dt, hist, n_hist))) return 0;
+    return chan_ws_first_spectrum(n_hist);
+}
+
+cudaError_t launch_chan_ws(const void *hist, const void *samples, long n_samples, long n_hist, acf_in_dtype dt,
+                           int n_sb, int N, const float *h, const float *bp, float scale, int out_kind, void *out,
+                           void *out_lo, long t_stride, long T, cudaStream_t s)
+{
+    const long m_begin = chan_ws_begin(dt, out_kind, N, t_stride, out, hist, n_hist);
     const long m_end = round_up(T, 64);
     if (m_end <= m_begin) return cudaSuccess;
     const int E = in_elem_bytes(dt);
@@ -908,9 +949,11 @@ cudaError_t launch_chan_ws(const void *samples, long n_samples, long n_hist, acf
     if (!enc) return cudaErrorNotSupported;
     WsParams P;
     std::memset(&P, 0, sizeof(P));
-    // fp16 output takes the tensor-core DFT (items of eight inputs)
-    const bool use_tc = out_kind == OUT_F16 && N % kTcNI == 0 && t_stride % 2 == 0 &&
-                        reinterpret_cast<uintptr_t>(out) % 4 == 0;
+    const bool use_tc = tc_variant(dt, out_kind, N, t_stride, out);
+    if (use_tc && m_begin == 0 && n_hist > 0) {
+        P.hist = hist;
+        P.n_hist = n_hist;
+    }
     const int NI = use_tc ? kTcNI : 16 / E;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)n_samples, (cuuint64_t)n_sb};
     cuuint64_t strides[2] = {(cuuint64_t)N * E, (cuuint64_t)n_samples * N * E};

@@ -35,6 +35,24 @@ def _np_complex(V):
     return V[..., 0].numpy().astype(np.float64) + 1j * V[..., 1].numpy().astype(np.float64)
 
 
+def _check_fp16_tc_bound(Xh, X32, w, sc, T):
+    """64 channels, fp16 output: the DFT runs on the tensor cores with the FIR
+    outputs y and the twiddles W rounded to fp16 (unit roundoff u = 2^-11)
+    and fp32 accumulation.  Per (input, spectrum):
+        |z_hat_c - z_c| <= (2u + u^2) sum_n |y_n| + 2^-15 sum_n |y_n|,
+    and by Parseval sum_n |y_n| <= 8 ||y||_2 = ||z||_2 over the 64
+    unweighted channels; the output rounding adds u |v| (v = scaled fp32
+    value)."""
+    C = X32.shape[1]
+    v = (X32 * sc)[..., :T]
+    wt = torch.as_tensor(w, dtype=torch.float32, device=X32.device).view(1, C, 1, 1)
+    zr, zi = X32[:, :, 0::2, :T] / wt, X32[:, :, 1::2, :T] / wt
+    nrm = torch.sqrt((zr * zr + zi * zi).sum(dim=1, keepdim=True))          # [sb, 1, N, T]
+    nrm2 = torch.repeat_interleave(nrm, 2, dim=2)                            # per re / im row
+    bound = v.abs() * 2.0 ** -11 + 1e-6 * v.abs().max() + (2.0 ** -10 + 2.0 ** -14) * (sc * wt).abs() * nrm2
+    assert ((Xh[..., :T].float() - v).abs() <= bound).all()
+
+
 # ---------------------------------------------------------------- channeliser
 @pytest.mark.parametrize("C,P,dtype,N,S", [
     (64, 16, "ci8", 96, 19532),       # the tiny single-station configuration
@@ -72,7 +90,7 @@ def test_channelise_fp16_split_reconstructs():
 
 
 @pytest.mark.parametrize("C", [64, 256])
-@pytest.mark.parametrize("dtype,N", [("ci16", 36), ("ci8", 40)])
+@pytest.mark.parametrize("dtype,N", [("ci16", 36), ("ci16", 48), ("ci8", 40)])
 @pytest.mark.parametrize("n_hist", [0, 500, 1023, 3000])
 def test_channelise_fast_paths_history_and_segments_vs_oracle(C, dtype, N, n_hist):
     """The 64-channel warp-specialised path (N a multiple of one 16-byte row
@@ -98,6 +116,18 @@ def test_channelise_fast_paths_history_and_segments_vs_oracle(C, dtype, N, n_his
         gc = got[:, 0::2, :T] + 1j * got[:, 1::2, :T]
         assert np.max(np.abs(gc - ref)) <= 2e-6 * np.max(np.abs(ref))
         assert np.all(got[:, :, T:(T + 63) // 64 * 64] == 0)
+    # fp16 output over the same history (64 channels: the tensor-core kernel
+    # reads a history shorter than one window itself)
+    sc = 0.25 if dtype == "ci16" else 4.0
+    Xh, _, Th = acf.channelise(x, C, P, out_kind="f16", hist=hist, scale=sc)
+    torch.cuda.synchronize()
+    assert Th == T
+    if C == 64 and N % 8 == 0:
+        _check_fp16_tc_bound(Xh, X, np.ones(C), sc, T)
+    else:
+        v = (X * sc)[..., :T]
+        assert ((Xh[..., :T].float() - v).abs() <= v.abs() * 2.0 ** -11 + 1e-6 * v.abs().max()).all()
+    assert (Xh[..., T:] == 0).all()
 
 
 @pytest.mark.parametrize("C", [64, 256])
@@ -131,18 +161,7 @@ def test_channelise_fast_paths_fp16_outputs_and_bandpass(C, dtype, N):
     if C == 256:
         assert torch.equal(Xh[..., :T], Xh3[..., :T])
     else:
-        # 64 channels, fp16 output: the DFT runs on the tensor cores with the
-        # FIR outputs y and the twiddles W rounded to fp16 (unit roundoff
-        # u = 2^-11) and fp32 accumulation.  Per (input, spectrum):
-        #   |z_hat_c - z_c| <= (2u + u^2) sum_n |y_n| + 2^-15 sum_n |y_n|
-        # and by Parseval sum_n |y_n| <= 8 ||y||_2 = ||z||_2 over the 64
-        # unweighted channels; the output rounding adds u |v|.
-        wt = torch.as_tensor(w, dtype=torch.float32, device=X32.device).view(1, C, 1, 1)
-        zr, zi = X32[:, :, 0::2, :T] / wt, X32[:, :, 1::2, :T] / wt
-        nrm = torch.sqrt((zr * zr + zi * zi).sum(dim=1, keepdim=True))          # [sb, 1, N, T]
-        nrm2 = torch.repeat_interleave(nrm, 2, dim=2)                            # per re / im row
-        bound = half_ulp + (2.0 ** -10 + 2.0 ** -14) * (sc * wt).abs() * nrm2
-        assert ((Xh[..., :T].float() - v).abs() <= bound).all()
+        _check_fp16_tc_bound(Xh, X32, w, sc, T)
     recon = Xh3[..., :T].float() + Xl3[..., :T].float()
     assert (recon - v).abs().max().item() <= 4e-6 * v.abs().max().item()
     assert (Xh[..., T:] == 0).all() and (Xl3[..., T:] == 0).all()
