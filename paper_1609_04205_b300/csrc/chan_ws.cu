@@ -885,6 +885,11 @@ cudaError_t launch_tc_t(WsParams &P, int grid, cudaStream_t s)
     auto kern = k_ppf64_tc<IN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
+    // a block's warps spread over the SM's four register-file partitions:
+    // refuse a build whose register count leaves no room for the whole block
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    if (fa.maxThreadsPerBlock < kTcThreads) return cudaErrorLaunchOutOfResources;
     kern<<<grid, kTcThreads, G::SMEM, s>>>(P);
     g_launches++;
     return cudaGetLastError();
