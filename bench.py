@@ -366,6 +366,46 @@ def time_batch(acf, torch, synth, pk, steps=10):
                          "raw jobs INT8 exact, channelised jobs split FP16; one CUDA-graph replay per run")
 
 
+def time_channeliser_alone(torch, x, w, pk, steps=5):
+    """The headline's channelisation (every subband, 64 channels x 16 taps, fp16
+    operand out, no history) launched by itself through acf_channelise on the
+    resident input: CUDA events around `steps` back-to-back calls."""
+    import ctypes
+    from paper_1609_04205_b300 import _lib as A
+    L = A.lib()
+    n_sb, S, N = x.shape[0], x.shape[1], x.shape[2]
+    C, P = w["n_channels"], w["n_taps"]
+    T = (S - P * C) // C + 1
+    ts = (T + 63) // 64 * 64
+    h = torch.as_tensor(prototype_of(P, C), device=x.device)
+    bp = torch.ones(C, dtype=torch.float32, device=x.device)
+    X = torch.empty((n_sb, C, 2 * N, ts), dtype=torch.float16, device=x.device)
+    To = ctypes.c_long(0)
+    run = lambda: A.check(L.acf_channelise(None, 0, A.ptr(x), S, A.DTYPES[w["dtype"]], n_sb, N, C, P, A.ptr(h),
+                                           A.ptr(bp), A.OUT_F16, A.ptr(X), None, ts, 0.125, ctypes.byref(To),
+                                           A.stream_handle(None)))
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nbytes = x.numel() * x.element_size() + X[..., :T].numel() * 2
+    del X
+    torch.cuda.empty_cache()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return dict(ms=ms, gbs=gbs, frac_hbm=gbs / pk["hbm"], bytes=nbytes, kernel="k_ppf64_tc")
+
+
+def prototype_of(P, C):
+    import paper_1609_04205_b300 as acf
+    return acf.prototype(P, C)
+
+
 def time_gain(acf, torch, pk, N=576, C=64, steps=20):
     """Gain forward (loss) + adjoint (gradient) in one pass over packed R and V:
     576 inputs, 64 channels, complex float32."""
@@ -612,6 +652,7 @@ def main():
     # channeliser HBM throughput (algorithmic bytes: ci16 in + fp16 out)
     out_bytes = n_sb * w["n_channels"] * 2 * N * statistics.median(main_r["T"]) * 2
     chan_gbs = (in_bytes + out_bytes) / (main_r["chan_ms"] * 1e-3) / 1e9
+    chan_alone = time_channeliser_alone(torch, x, w, pk)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -698,7 +739,10 @@ def main():
                 roofline=roof, clocks=clocks, gpu_launches=main_r["launches"],
                 xengine_tuning=main_r["xengine_tuning"],
                 channeliser=dict(ms=main_r["chan_ms"], gbs=chan_gbs, frac_hbm=chan_gbs / pk["hbm"],
-                                 bytes=in_bytes + out_bytes),
+                                 bytes=in_bytes + out_bytes,
+                                 note="inside the step: history head and filter-state copy included, at the step's "
+                                      "power-capped clock; `alone` is the same channelisation launched by itself"),
+                channeliser_alone=chan_alone,
                 e2e=e2e, cpu_baseline=cpu, accuracy=accuracy, modes=extra, post=post_r, ragged_batch=batch_r,
                 gain=gain_r)
     if rank == 0:
