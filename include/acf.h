@@ -110,12 +110,14 @@ acf_status acf_push_block(acf_ctx *ctx, const void *samples, long n_samples,
                           acf_stream_t stream);
 
 /* Same as acf_push_block but `samples` is HOST memory (pinned for best
- * speed).  Subbands are copied host->device through a double-buffered
- * staging area on `stream` and a private copy stream, overlapping each copy
- * with the channeliser of the previous subband (Sec. 4.2, "asynchronous host
- * to device transfers overlapping with compute").  The call returns once the
- * work is enqueued; the host buffer must stay valid until `stream` reaches
- * this point. */
+ * speed).  Subbands are copied host->device into a device staging area on a
+ * private copy stream, each subband's channeliser waiting only for its own
+ * copy (Sec. 4.2, "asynchronous host to device transfers overlapping with
+ * compute").  A push's copies wait only for the previous host push's kernels
+ * that read the staging, so they also overlap the previous push's X-engine
+ * and a visibility read-back enqueued after it.  The call returns once the
+ * work is enqueued; the host buffer must stay valid and unchanged until
+ * `stream` reaches this point. */
 acf_status acf_push_block_host(acf_ctx *ctx, const void *samples, long n_samples,
                                acf_stream_t stream);
 

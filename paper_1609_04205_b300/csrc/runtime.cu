@@ -68,6 +68,8 @@ struct acf_ctx {
     void *d_stage = nullptr;      // host-push staging [n_sb][max_samples][N]
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> ev_copied;
+    cudaEvent_t ev_stage_free = nullptr;   // recorded after the last kernel that reads the staging
+    bool stage_pending = false;
     TcPlan *plan = nullptr;
     int variant = 0;              // 0: one SM per 128x256 tile; 1: SM pairs per 256x256 tile
     TcTuning tun;                 // N tile, time split, order (pair mirrors `variant`)
@@ -535,6 +537,12 @@ static acf_status push_common(acf_ctx *c, const void *dev_samples, long S, cudaS
         c->H = newH;
         (void)L;
     }
+    if (per_subband_ready && c->ev_stage_free) {
+        // the staging's readers (transposes or channelisers and the history
+        // copies) are all enqueued: the next host push may refill it after them
+        if ((e = cudaEventRecord(c->ev_stage_free, s)) != cudaSuccess) return cuda_fail(c, e, "record staging");
+        c->stage_pending = true;
+    }
     if (c->timing) cudaEventRecord(c->ev[1], s);
     if (T > 0) {
         // the first X-engine pass of an integration overwrites V when one work item owns
@@ -602,14 +610,16 @@ acf_status acf_push_block_host(acf_ctx *c, const void *samples, long n_samples, 
         c->ev_copied.resize(c->n_sb);
         for (auto &ev : c->ev_copied)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if ((e = cudaEventCreateWithFlags(&c->ev_stage_free, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "event");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the copy stream must not overwrite staging still read by earlier work on `s`
-    cudaEvent_t start;
-    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
-    cudaEventRecord(start, s);
-    cudaStreamWaitEvent(c->copy_stream, start, 0);
-    cudaEventDestroy(start);
+    // the copies must not overwrite staging that the previous host push's
+    // kernels still read; they need not wait for anything else on `s` (the
+    // previous X-engine, a visibility read-back), so this push's host-to-device
+    // copies overlap that work
+    if (c->stage_pending && (e = cudaStreamWaitEvent(c->copy_stream, c->ev_stage_free, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "wait staging");
     for (int sb = 0; sb < c->n_sb; ++sb) {
         e = cudaMemcpyAsync(static_cast<char *>(c->d_stage) + sb * per_sb, static_cast<const char *>(samples) + sb * per_sb,
                             per_sb, cudaMemcpyHostToDevice, c->copy_stream);
@@ -757,6 +767,7 @@ acf_status acf_destroy(acf_ctx *c)
     cudaFree(c->d_stage);
     cudaFree(c->d_delay_tab);
     for (auto ev : c->ev_copied) cudaEventDestroy(ev);
+    if (c->ev_stage_free) cudaEventDestroy(c->ev_stage_free);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->plan) tc_plan_destroy(c->plan);
     delete c;
