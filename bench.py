@@ -456,6 +456,7 @@ def aggregate(ms_local, ops_local, device="cpu"):
 def profile_case_kernels(which):
     """Small cases of single kernels for ncu captures (a few GB on the device):
     sigma_clip -- acf_sigma_clip on four A-12 subbands of visibilities (1.36 GB);
+    batch -- the ragged batch: autotune, graph capture, then two replays;
     gain -- acf_gain_forward on 576 inputs x 64 channels;
     chan256 -- acf_channelise, 256 channels x 16 taps, 1152 inputs x 48,828 ci8
     samples to split fp16.  Four calls each."""
@@ -464,6 +465,7 @@ def profile_case_kernels(which):
     import torch
 
     import paper_1609_04205_b300 as acf
+    import synth
     from paper_1609_04205_b300 import _lib as A
     L = A.lib()
     hs = A.stream_handle(None)
@@ -476,6 +478,8 @@ def profile_case_kernels(which):
             A.check(L.acf_sigma_clip(A.ptr(V), A.ptr(flags), n_sb, C, N, 5.0, 3.0, hs))
     elif which == "gain":
         time_gain(acf, torch, peaks(), steps=1)
+    elif which == "batch":
+        time_batch(acf, torch, synth, peaks(), steps=2)
     elif which == "chan256":
         N, S, C, P = 1152, 48828, 256, 16
         x = torch.randint(-100, 100, (1, S, N, 2), dtype=torch.int8, device="cuda", generator=g)
@@ -499,7 +503,7 @@ def profile_case(mode):
 
     import paper_1609_04205_b300 as acf
     import synth
-    if mode in ("sigma_clip", "gain", "chan256"):
+    if mode in ("sigma_clip", "gain", "chan256", "batch"):
         return profile_case_kernels(mode)
     w = dict(synth.WORKLOADS["a6" if mode == "int8" else "a12"])
     w["n_subbands"] = 1
@@ -569,7 +573,7 @@ def main():
                     help="run only the post-correlation kernels on the A-12 visibility set (profiling)")
     ap.add_argument("--probe", action="store_true",
                     help="tensor-pipe rate with operands resident in shared memory (one JSON line), then exit")
-    ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8", "sigma_clip", "gain", "chan256"],
+    ap.add_argument("--profile-case", choices=["fp16", "fp16x3", "fp32", "int8", "sigma_clip", "gain", "chan256", "batch"],
                     default=None,
                     help="small case for ncu captures: one subband of the default workload (one raw "
                          "A-6 subband for int8), warm-up plus three pushes; or one post-correlation, gain "
