@@ -215,6 +215,13 @@ acf_status acf_prototype(int n_taps, int n_channels, float *h_out);
  *            row; element float32 (out_kind 0), fp16 (1) or fp16 hi with the
  *            fp16 residual in `out_lo` (2).  Values are scaled by `scale`
  *            before fp16 rounding.  Spectra [T, roundup(T, 64)) are zeroed.
+ *            Precision: float32 and split output carry the fp32 FFT.  fp16
+ *            output with 64 channels, 16 taps, ci8/ci16 input and a multiple
+ *            of 8 inputs computes the DFT on the tensor cores with the FIR
+ *            outputs and the twiddles rounded to fp16 (fp32 accumulation);
+ *            the extra error is at most (2^-10 + 2^-14) ||z||_2 per value,
+ *            ||z||_2 the spectrum's norm over the 64 unweighted channels,
+ *            times the channel's weight and `scale`. 
  *   *n_spectra_out (host) receives T = floor((n_hist + n_samples - (P-1) C) / C)
  *   (0 when negative).  t_stride must be >= roundup(T, 64) and a multiple of 64.
  * n_channels in {16, 64, 256}; use acf_transpose_raw for n_channels == 1. */
