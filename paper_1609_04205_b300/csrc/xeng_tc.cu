@@ -372,6 +372,23 @@ __device__ __forceinline__ void flush_tile(const JobDev &J, int p, int i, int jb
                     }
                 }
             }
+        } else if (J.store && nval == 32) {
+            // a whole run (every tile off the diagonal): 16-byte stores, with a
+            // single at each end when the run starts at an odd element
+            float2 *dst = static_cast<float2 *>(J.V) + (prow + jbase);
+            const auto mf = [&](int k) { return __uint_as_float(m[k]); };
+            if (((prow + jbase) & 1) == 0) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    *reinterpret_cast<float4 *>(dst + 2 * k) = make_float4(mf(4 * k), mf(4 * k + 1), mf(4 * k + 2), mf(4 * k + 3));
+            } else {
+                dst[0] = make_float2(mf(0), mf(1));
+#pragma unroll
+                for (int k = 0; k < 15; ++k)
+                    *reinterpret_cast<float4 *>(dst + 2 * k + 1) =
+                        make_float4(mf(4 * k + 2), mf(4 * k + 3), mf(4 * k + 4), mf(4 * k + 5));
+                dst[31] = make_float2(mf(62), mf(63));
+            }
         } else {
             float2 *dst = static_cast<float2 *>(J.V) + (prow + jbase);
             // pair elements on 16-byte boundaries: a leading single when the run starts odd
