@@ -110,10 +110,53 @@ k_corner_turn(const T *__restrict__ hist, long n_hist, const T *__restrict__ in,
     }
 }
 
+// The same corner turn for 2-byte elements (complex int8) when the input rows
+// allow 4-byte access (N even, aligned buffers): 64 x 64 tiles, each warp
+// loading 64 inputs of one stream row and storing 64 samples of one input row
+// as single 128-byte lines.  The odd row pitch of 65 halfwords keeps the
+// column reads of the second phase free of bank conflicts.  A pair whose
+// second sample lies past the stream is padded with zero inside the row pitch.
+__global__ void __launch_bounds__(256)
+k_corner_turn16(const uint16_t *__restrict__ hist, long n_hist, const uint16_t *__restrict__ in, long n_samples,
+                int N, uint16_t *__restrict__ out, long ld)
+{
+    __shared__ uint16_t tile[64][65];
+    const int sb = blockIdx.z;
+    const long q0 = (long)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    const long L = n_hist + n_samples;
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = n0 + 2 * tx;
+#pragma unroll
+    for (int r = w; r < 64; r += 8) {
+        const long q = q0 + r;
+        uint32_t v = 0;
+        if (q < L && n < N) {
+            const uint16_t *src = q < n_hist ? hist + ((long)sb * n_hist + q) * N + n
+                                             : in + ((long)sb * n_samples + (q - n_hist)) * N + n;
+            v = __ldg(reinterpret_cast<const unsigned int *>(src));
+        }
+        tile[r][2 * tx] = (uint16_t)(v & 0xffffu);
+        tile[r][2 * tx + 1] = (uint16_t)(v >> 16);
+    }
+    __syncthreads();
+    const long q = q0 + 2 * tx;
+#pragma unroll
+    for (int c = w; c < 64; c += 8) {
+        const int nc = n0 + c;
+        if (nc < N && q < L) {
+            const uint32_t v = (uint32_t)tile[2 * tx][c] | ((uint32_t)tile[2 * tx + 1][c] << 16);
+            *reinterpret_cast<uint32_t *>(out + ((long)sb * N + nc) * ld + q) = v;
+        }
+    }
+}
+
 // IM: samples come from the corner-turned rows xim[subband][input][q] (pitch
 // ld, history included) instead of the [time][input] stream.
+// The corner-turned form needs fewer registers (no strided sample addresses):
+// capped for two blocks per SM, it spills at most 12 bytes.
 template <typename IN, int OUTK, bool IM>
-__global__ void __launch_bounds__(kC, 1)
+__global__ void __launch_bounds__(kC, IM ? 2 : 1)
 k_chan256(const IN *__restrict__ hist, long n_hist, const IN *__restrict__ in, long n_samples, int N,
           const float *__restrict__ h, const float *__restrict__ bp, const float2 *__restrict__ tw_g,
           void *__restrict__ out, void *__restrict__ out_lo, long t_stride, float scale, long T, long m_per_block,
@@ -300,9 +343,17 @@ cudaError_t launch_dt(int out_kind, const void *hist, long n_hist, const void *s
         using W = typename std::conditional<sizeof(IN) == 2, uint16_t, uint32_t>::type;
         ld = chan256_row_pitch(n_hist, n_samples);
         const long L = n_hist + n_samples;
-        const dim3 g((unsigned)((L + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)n_sb);
-        k_corner_turn<W><<<g, 256, 0, s>>>(static_cast<const W *>(hist), n_hist, static_cast<const W *>(samples),
-                                          n_samples, N, static_cast<W *>(scratch), ld);
+        auto a4 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 4 == 0; };
+        if (sizeof(IN) == 2 && N % 2 == 0 && a4(samples) && a4(scratch) && (!hist || a4(hist))) {
+            const dim3 g((unsigned)((L + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)n_sb);
+            k_corner_turn16<<<g, 256, 0, s>>>(static_cast<const uint16_t *>(hist), n_hist,
+                                              static_cast<const uint16_t *>(samples), n_samples, N,
+                                              static_cast<uint16_t *>(scratch), ld);
+        } else {
+            const dim3 g((unsigned)((L + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)n_sb);
+            k_corner_turn<W><<<g, 256, 0, s>>>(static_cast<const W *>(hist), n_hist, static_cast<const W *>(samples),
+                                              n_samples, N, static_cast<W *>(scratch), ld);
+        }
         g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -197,6 +197,37 @@ def test_correlator_streaming_pushes_ci16(C):
             assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
 
 
+@pytest.mark.parametrize("N", [70, 33])
+def test_correlator_streaming_256ch_ci8_corner_turn(N):
+    """256-channel context on complex int8 over ragged pushes: each push is
+    corner-turned (history, then the samples) into per-input rows before the
+    filter bank reads them.  An even input count takes the 4-byte, 64 x 64
+    tile form (N = 70 spans two input tiles, the second ragged), an odd one
+    the 32 x 32 form; split FP16 against the oracle's stream partition."""
+    _dev()
+    P, C = 16, 256
+    pushes = [4100, 256 * 7 + 3, 9000, 601, 5555]
+    S = sum(pushes)
+    sky = synth.make_sky(N, 2, (0.1, 0.4), 78)
+    x = synth.voltages(N, S, 2, "ci8", 16.0, sky, 78, device="cuda")
+    xs = x.cpu().numpy()
+    with acf.Correlator(N, 2, C, P, 2, "fp16x3", "ci8", max(pushes)) as c:
+        outs = []
+        t0 = 0
+        for n in pushes:
+            c.push(x[:, t0:t0 + n].contiguous())
+            t0 += n
+            V = c.visibilities()
+            if V is not None:
+                outs.append(V.clone())
+        assert len(outs) == 2
+    torch.cuda.synchronize()
+    for sb in range(2):
+        ref = oracle.correlator(xs[sb], P, C, push_sizes=pushes, n_integrate=2)
+        for k in range(2):
+            assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
+
+
 @pytest.mark.parametrize("N,S,scale", [(8, 64, 1.0), (64, 1000, 1.0), (72, 777, 1.0), (96, 5000, 0.5),
                                          (1152, 300, 1.0), (5, 130, 1.0)])
 def test_transpose_raw_ci8_fp16_exact(N, S, scale):
