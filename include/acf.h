@@ -398,6 +398,20 @@ acf_status acf_batch_run(acf_batch *b, const void *const *inputs, void *const *o
 /* Tile settings chosen by the planner/autotuner: n_tile (128 or 256 real rows)
  * and the time split factor. */
 acf_status acf_batch_query(const acf_batch *b, int *n_tile, int *k_split, int *n_work_items);
+
+/* The rest of the chosen plan: pair = 1 when CTA pairs share 256 x 256 tiles
+ * (tcgen05 cta_group::2), 0 for one SM per 128-row tile; order = 0 (jobs as
+ * given), 1 (largest job first) or 2 (largest first, with the items of
+ * short-integration jobs interleaved among the others so that each SM's
+ * flush-bound and MMA-bound tiles overlap).  NULL outputs are skipped. */
+acf_status acf_batch_query_plan(const acf_batch *b, int *pair, int *order);
+
+/* Choose the plan instead of the autotuner: pair 0 or 1 (pair = 1 needs
+ * n_tile 256), n_tile 128 or 256, k_split 1, 2 or 4, order 0, 1 or 2 (as
+ * acf_batch_query_plan reports them).  The next acf_batch_run rebuilds the
+ * work list and re-captures its graph.  ACF_EINVAL for other values (the
+ * batch keeps its plan). */
+acf_status acf_batch_set_plan(acf_batch *b, int pair, int n_tile, int k_split, int order);
 acf_status acf_batch_destroy(acf_batch *b);
 const char *acf_batch_last_error(const acf_batch *b);
 

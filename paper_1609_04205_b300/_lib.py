@@ -26,7 +26,7 @@ EXPORTS = [
     "acf_get_visibilities", "acf_visibilities_device", "acf_query", "acf_destroy", "acf_last_error",
     "acf_status_string", "acf_prototype", "acf_channelise", "acf_transpose_raw", "acf_xengine",
     "acf_gain_forward", "acf_gain_backward", "acf_batch_create", "acf_batch_run", "acf_batch_query",
-    "acf_batch_destroy", "acf_batch_last_error", "acf_launch_count", "acf_device_status", "acf_version",
+    "acf_batch_query_plan", "acf_batch_set_plan", "acf_batch_destroy", "acf_batch_last_error", "acf_launch_count", "acf_device_status", "acf_version",
     "acf_enable_timing", "acf_last_timing", "acf_gain_forward_noalloc", "acf_set_xengine_variant",
     "acf_delay_compensate", "acf_set_delays", "acf_integrate_channels", "acf_sigma_clip",
     "acf_lost_sample_weights", "acf_reweight", "acf_tune", "acf_query_xengine", "acf_probe_tensor_peak",
@@ -87,6 +87,8 @@ def lib():
         "acf_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(Job), I, I], I),
         "acf_batch_run": ([P, PP, PP, P], I),
         "acf_batch_query": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "acf_batch_query_plan": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "acf_batch_set_plan": ([P, I, I, I, I], I),
         "acf_batch_destroy": ([P], I),
         "acf_batch_last_error": ([P], ctypes.c_char_p),
         "acf_launch_count": ([], ctypes.c_longlong),

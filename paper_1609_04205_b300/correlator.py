@@ -247,7 +247,13 @@ class Batch:
     def query(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         A.check(self._L.acf_batch_query(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), batch=self._h)
-        return dict(n_tile=a.value, k_split=b.value, n_items=c.value)
+        pr, od = ctypes.c_int(), ctypes.c_int()
+        A.check(self._L.acf_batch_query_plan(self._h, ctypes.byref(pr), ctypes.byref(od)), batch=self._h)
+        return dict(n_tile=a.value, k_split=b.value, n_items=c.value, pair=pr.value, order=od.value)
+
+    def set_plan(self, pair, n_tile, k_split, order):
+        """Fix the X-engine plan (see acf_batch_set_plan) instead of autotuning."""
+        A.check(self._L.acf_batch_set_plan(self._h, int(pair), int(n_tile), int(k_split), int(order)), batch=self._h)
 
     def close(self):
         if getattr(self, "_h", None):

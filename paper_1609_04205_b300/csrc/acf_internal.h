@@ -113,7 +113,7 @@ struct TcPlan;            // opaque: tensor maps + work list on the device
 struct TcTuning {
     int n_tile = 256;     // real rows per N tile: 128 or 256
     int k_split = 1;      // time split factor per tile (atomically reduced)
-    int order = 0;        // 0: problem-major, 1: longest-first
+    int order = 0;        // 0: problem-major, 1: longest-first, 2: longest-first with short-K items interleaved
     int pair = 0;         // 1: two-SM kernel (256x256 tiles on CTA pairs, cta_group::2)
 };
 cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, TcPlan **out,

@@ -180,7 +180,7 @@ static void autotune(acf_batch *b)
     for (int pair : {1, 0})
     for (int nt : {256, 128})
         for (int ks : {1, 2, 4})
-            for (int order : {1, 0}) {
+            for (int order : {2, 1, 0}) {
                 if (pair && nt == 128) continue;   // the pair kernel always uses 256-row tiles
                 TcTuning t;
                 t.pair = pair;
@@ -359,6 +359,32 @@ acf_status acf_batch_query(const acf_batch *b, int *n_tile, int *k_split, int *n
     if (n_tile) *n_tile = b->tun.n_tile;
     if (k_split) *k_split = b->tun.k_split;
     if (n_items) *n_items = b->plan ? tc_plan_items(b->plan) : 0;
+    return ACF_OK;
+}
+
+acf_status acf_batch_query_plan(const acf_batch *b, int *pair, int *order)
+{
+    if (!b) return ACF_EINVAL;
+    if (pair) *pair = b->tun.pair;
+    if (order) *order = b->tun.order;
+    return ACF_OK;
+}
+
+acf_status acf_batch_set_plan(acf_batch *b, int pair, int n_tile, int k_split, int order)
+{
+    if (!b) return ACF_EINVAL;
+    if ((pair != 0 && pair != 1) || (n_tile != 128 && n_tile != 256) || (pair && n_tile != 256) ||
+        (k_split != 1 && k_split != 2 && k_split != 4) || order < 0 || order > 2)
+        return bf(b, ACF_EINVAL, "plan: pair 0/1 (pair needs n_tile 256), n_tile 128/256, k_split 1/2/4, order 0..2");
+    cudaDeviceSynchronize();
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->tun.pair = pair;
+    b->tun.n_tile = n_tile;
+    b->tun.k_split = k_split;
+    b->tun.order = order;
     return ACF_OK;
 }
 

@@ -72,6 +72,7 @@ struct TcParams {
     int n_jobs;
     int n_items;
     int *err;
+    const int *perm;      // work position -> item (interleaved order), or nullptr
 };
 
 struct Item {
@@ -217,7 +218,11 @@ __host__ __device__ inline int tiles_per_problem(int N, int nt) {
     return t;
 }
 
+// PERM: the work position is mapped through the plan's interleaved order (a
+// separate instantiation, so the plain order's kernels carry no extra load).
+template <bool PERM>
 __device__ __forceinline__ bool decode_item(const TcParams &P, int item, Item &it) {
+    if (PERM) item = __ldg(P.perm + item);
     int j = 0;
     while (j + 1 < P.n_jobs && item >= P.jobs[j + 1].item_begin) ++j;
     const JobDev &J = P.jobs[j];
@@ -411,6 +416,7 @@ __device__ __forceinline__ void flush_tile(const JobDev &J, int p, int i, int jb
     }
 }
 
+template <bool PERM>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant__ TcParams P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             bool ok = true;
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
                 Item it;
-                if (!decode_item(P, item, it)) continue;
+                if (!decode_item<PERM>(P, item, it)) continue;
                 const JobDev &J = P.jobs[it.job];
                 const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
                 const int rowA = it.p * 2 * J.N + it.bi * kBM;
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
             bool ok = true;
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
                 Item it;
-                if (!decode_item(P, item, it)) continue;
+                if (!decode_item<PERM>(P, item, it)) continue;
                 const JobDev &J = P.jobs[it.job];
                 const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
                 const uint32_t idesc = idesc_f16(J.nt);
@@ -533,7 +539,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc(const __grid_constant
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             Item it;
-            if (!decode_item(P, item, it)) continue;
+            if (!decode_item<PERM>(P, item, it)) continue;
             const JobDev &J = P.jobs[it.job];
             const bool exact = J.mode == ACF_X_INT8;
             const bool active = half * 128 < J.nt;
@@ -634,7 +640,9 @@ __host__ __device__ inline int sq_tiles_per_problem(int N) {
     return nb * (nb + 1) / 2;
 }
 
+template <bool PERM>
 __device__ __forceinline__ bool decode_item2(const TcParams &P, int item, Item &it) {
+    if (PERM) item = __ldg(P.perm + item);
     int j = 0;
     while (j + 1 < P.n_jobs && item >= P.jobs[j + 1].item_begin) ++j;
     const JobDev &J = P.jobs[j];
@@ -656,6 +664,7 @@ __device__ __forceinline__ bool decode_item2(const TcParams &P, int item, Item &
     return it.k0 < it.k1;
 }
 
+template <bool PERM>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constant__ TcParams P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -719,7 +728,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
             bool ok = true;
             for (int item = cid; item < P.n_items && ok; item += ncl) {
                 Item it;
-                if (!decode_item2(P, item, it)) continue;
+                if (!decode_item2<PERM>(P, item, it)) continue;
                 const JobDev &J = P.jobs[it.job];
                 const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
                 const int rowA = it.p * 2 * J.N + it.bi * kBM2 + (int)rank * kBM;
@@ -763,7 +772,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
             const uint32_t ring = smem_u32(smem);
             for (int item = cid; item < P.n_items && ok; item += ncl) {
                 Item it;
-                if (!decode_item2(P, item, it)) continue;
+                if (!decode_item2<PERM>(P, item, it)) continue;
                 const JobDev &J = P.jobs[it.job];
                 const int spk = J.mode == ACF_X_FP16x3 ? 2 : 1;
                 const long steps = (it.k1 - it.k0) / kBK;
@@ -798,7 +807,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_xeng_tc2(const __grid_constan
         bool ok = true;
         for (int item = cid; item < P.n_items && ok; item += ncl) {
             Item it;
-            if (!decode_item2(P, item, it)) continue;
+            if (!decode_item2<PERM>(P, item, it)) continue;
             const JobDev &J = P.jobs[it.job];
             const bool exact = J.mode == ACF_X_INT8;
             const long steps = (it.k1 - it.k0) / kBK;
@@ -876,7 +885,42 @@ struct TcPlan {
     int grid = 0;
     size_t smem = 0;
     bool pair = false;       // two-SM kernel (CTA pairs, cta_group::2)
+    int *d_perm = nullptr;   // device copy of params.perm (interleaved order)
 };
+
+// Interleaved work order: items whose K range spans at most four K steps
+// (short-K jobs, e.g. 256 channels of a 0.25 s integration) are flush-bound,
+// the rest MMA-bound.  The persistent kernels hand work position w to worker
+// w mod W (W = CTAs or CTA pairs), so alternating chunks of W long items with
+// the proportional number of W-item chunks of short ones gives every worker
+// a mix: the TMEM double buffer then overlaps a short item's flush with a
+// long item's MMAs.  Returns an empty vector when either class is empty.
+static std::vector<int> interleave_items(const TcParams &P, int workers)
+{
+    std::vector<int> sh, lg;
+    for (int jj = 0; jj < P.n_jobs; ++jj) {
+        const JobDev &D = P.jobs[jj];
+        const long K64 = round_up(D.n_time, 64);
+        const long per = round_up((K64 + D.k_split - 1) / D.k_split, 64);
+        std::vector<int> &v = per <= 4 * kBK ? sh : lg;
+        const int cnt = D.tiles_pp * D.k_split * D.n_problems;
+        for (int k = 0; k < cnt; ++k) v.push_back(D.item_begin + k);
+    }
+    std::vector<int> perm;
+    if (sh.empty() || lg.empty() || workers < 1) return perm;
+    perm.reserve(sh.size() + lg.size());
+    const double ratio = (double)sh.size() / (double)lg.size();   // short chunks per long chunk
+    size_t si = 0, li = 0;
+    double credit = 0.0;
+    while (li < lg.size()) {
+        for (int k = 0; k < workers && li < lg.size(); ++k) perm.push_back(lg[li++]);
+        credit += ratio;
+        for (; credit >= 1.0 && si < sh.size(); credit -= 1.0)
+            for (int k = 0; k < workers && si < sh.size(); ++k) perm.push_back(sh[si++]);
+    }
+    while (si < sh.size()) perm.push_back(sh[si++]);
+    return perm;
+}
 
 bool tc_supported(int device)
 {
@@ -906,7 +950,7 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
     auto cost = [&](int j) {
         return (double)jobs[j].N * jobs[j].N * jobs[j].n_time * (jobs[j].mode == ACF_X_FP16x3 ? 3 : 1);
     };
-    if (tun.order == 1) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    if (tun.order >= 1) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     int items = 0;
     for (int jj = 0; jj < n_jobs; ++jj) {
         const TcJob &J = jobs[order[jj]];
@@ -960,8 +1004,9 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     p->smem = (size_t)kSlots * kSlotBytes + 1024;
     static_assert(kSlots * kSlotBytes == kSlots2 * kSlotBytes2, "both kernels use the same shared memory");
-    cudaError_t e = cudaFuncSetAttribute(p->pair ? k_xeng_tc2 : k_xeng_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p->smem);
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {k_xeng_tc2<false>, k_xeng_tc2<true>, k_xeng_tc<false>, k_xeng_tc<true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (e != cudaSuccess) {
         delete p;
         if (err) *err = "cudaFuncSetAttribute(max dynamic smem) failed";
@@ -984,9 +1029,33 @@ cudaError_t tc_plan_create(const TcJob *jobs, int n_jobs, const TcTuning &tun, T
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_xeng_tc2, &cfg) == cudaSuccess && n > 0) clusters = std::min(clusters, n);
+        if (cudaOccupancyMaxActiveClusters(&n, k_xeng_tc2<false>, &cfg) == cudaSuccess && n > 0)
+            clusters = std::min(clusters, n);
         cudaGetLastError();
         p->grid = 2 * std::max(1, std::min(items, clusters));
+    }
+    if (tun.order == 2) {
+        const std::vector<int> perm = interleave_items(p->params, p->pair ? p->grid / 2 : p->grid);
+        if (!perm.empty()) {
+            // a permutation of the work items, each exactly once
+            std::vector<char> seen(items, 0);
+            bool okp = (int)perm.size() == items;
+            for (int v : perm) okp = okp && v >= 0 && v < items && !seen[v]++;
+            if (!okp) {
+                delete p;
+                if (err) *err = "tensor-core plan: bad interleaved order";
+                return cudaErrorUnknown;
+            }
+            if ((e = cudaMalloc(&p->d_perm, perm.size() * sizeof(int))) != cudaSuccess ||
+                (e = cudaMemcpy(p->d_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                cudaFree(p->d_perm);
+                delete p;
+                if (err) *err = "tensor-core plan: work order copy failed";
+                return e;
+            }
+            p->params.perm = p->d_perm;
+        }
     }
     *out = p;
     return cudaSuccess;
@@ -1019,7 +1088,8 @@ cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
 {
     if (p->params.n_items == 0) return cudaSuccess;
     if (!p->pair) {
-        k_xeng_tc<<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
+        if (p->params.perm) k_xeng_tc<true><<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
+        else k_xeng_tc<false><<<p->grid, kThreadsTc, p->smem, s>>>(p->params);
         g_launches++;
         return cudaGetLastError();
     }
@@ -1035,7 +1105,8 @@ cudaError_t tc_plan_launch(const TcPlan *p, cudaStream_t s)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_xeng_tc2, p->params);
+    cudaError_t e = p->params.perm ? cudaLaunchKernelEx(&cfg, k_xeng_tc2<true>, p->params)
+                                   : cudaLaunchKernelEx(&cfg, k_xeng_tc2<false>, p->params);
     g_launches++;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1156,6 +1227,10 @@ cudaError_t probe_tensor_peak(long k_steps, double *tflops, float *ms_out)
 }
 
 int tc_plan_items(const TcPlan *p) { return p->params.n_items; }
-void tc_plan_destroy(TcPlan *p) { delete p; }
+void tc_plan_destroy(TcPlan *p)
+{
+    if (p && p->d_perm) cudaFree(p->d_perm);
+    delete p;
+}
 
 }  // namespace acf

@@ -555,6 +555,43 @@ def test_batch_ragged_mixed_modes():
     b.close()
 
 
+@pytest.mark.parametrize("pair,n_tile,k_split,order", [(1, 256, 1, 2), (0, 128, 2, 2), (0, 256, 1, 1), (1, 256, 4, 0)])
+def test_batch_fixed_plans_match_oracle(pair, n_tile, k_split, order):
+    """Plans fixed through acf_batch_set_plan.  Order 2 interleaves the tiles of
+    the short-integration jobs (256 channels, 4 and 7 spectra: one K step)
+    among those of the raw and 64-channel jobs, through a work-order table;
+    every plan, CTA pairs or one SM per tile, gives the oracle's result
+    (raw jobs bit-exact), on the captured graph and its replay."""
+    _dev()
+    jobs = [dict(n_inputs=70, n_channels=256, n_taps=16, n_samples=256 * 19),
+            dict(n_inputs=150, n_channels=1, n_taps=1, n_samples=5000),
+            dict(n_inputs=33, n_channels=256, n_taps=16, n_samples=256 * 22),
+            dict(n_inputs=96, n_channels=64, n_taps=16, n_samples=64 * 315)]
+    b = acf.Batch(jobs, autotune=False)
+    b.set_plan(pair, n_tile, k_split, order)
+    q = b.query()
+    assert (q["pair"], q["n_tile"], q["k_split"], q["order"]) == (pair, n_tile, k_split, order)
+    ins = [synth.voltages(j["n_inputs"], j["n_samples"], 1, "ci8", 16.0, None, 90 + k, device="cuda")[0]
+           for k, j in enumerate(jobs)]
+    outs = b.outputs()
+    refs = {}
+    for rep in range(2):
+        b.run(ins, outs)
+        torch.cuda.synchronize()
+        for k, j in enumerate(jobs):
+            x = ins[k].cpu().numpy()
+            if j["n_channels"] == 1:
+                assert np.array_equal(outs[k][0].cpu().numpy(), oracle.correlate_int(x))
+            else:
+                if k not in refs:
+                    refs[k] = oracle.correlator(x, j["n_taps"], j["n_channels"])[0]
+                assert norm_err(_np_complex(torch.view_as_complex(outs[k])), refs[k], j["n_inputs"]) <= TOL_FP32
+    with pytest.raises(acf.AcfError):
+        b.set_plan(1, 128, 1, 0)          # CTA pairs always use 256-row tiles
+    assert b.query()["order"] == order
+    b.close()
+
+
 def test_batch_autotune_picks_valid_tiles():
     _dev()
     jobs = [dict(n_inputs=64, n_channels=1, n_taps=1, n_samples=2000),
