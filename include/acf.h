@@ -357,9 +357,9 @@ acf_status acf_gain_backward(const void *R, const void *V, const void *g, int n_
  *     channels: m (m + 1) / 2 * n_channels) -- are rejected with ACF_EINVAL
  *     before anything is enqueued; acf_gain_forward handles them.
  *   - The first call on a device looks up the array's device address (no
- *     allocation) and keeps it; make that first call before any stream
- *     capture.  cudaDeviceReset unloads the library's device image and would
- *     leave the kept address stale: do not reset the device between calls.
+ *     allocation) and keeps it.  cudaDeviceReset unloads the library's
+ *     device image and would leave the kept address stale: do not reset the
+ *     device between calls.
  *   - All calls share the array, so calls that may overlap on the GPU (on
  *     different streams without ordering) race; serialise them.
  *   - Each call rewrites the partials it reads (the array keeps the last
