@@ -65,12 +65,13 @@ cudaError_t launch_chan256(const void *hist, long n_hist, const void *samples, l
 // inputs, 16-byte aligned samples).  It produces spectra
 // [chan_ws_begin(...), roundup(T, 64)); the spectra before that reach into
 // the history and are left to the generic kernel.  The tensor-core variant
-// (fp16 output) reads a history shorter than one window itself and begins at
-// spectrum 0; otherwise the range begins at chan_ws_first_spectrum(n_hist).
+// (fp16 and split fp16 output) reads a history shorter than one window itself
+// and begins at spectrum 0; otherwise the range begins at
+// chan_ws_first_spectrum(n_hist).
 bool chan_ws_supported(acf_in_dtype dt, int C, int P, int N, const void *samples, long n_samples);
 long chan_ws_first_spectrum(long n_hist);
-long chan_ws_begin(acf_in_dtype dt, int out_kind, int N, long t_stride, const void *out, const void *hist,
-                   long n_hist);
+long chan_ws_begin(acf_in_dtype dt, int out_kind, int N, long t_stride, const void *out, const void *out_lo,
+                   const void *hist, long n_hist);
 cudaError_t launch_chan_ws(const void *hist, const void *samples, long n_samples, long n_hist, acf_in_dtype dt,
                            int n_sb, int N, const float *h, const float *bp, float scale, int out_kind, void *out,
                            void *out_lo, long t_stride, long T, cudaStream_t s);

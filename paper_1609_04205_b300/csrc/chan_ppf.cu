@@ -448,7 +448,7 @@ cudaError_t launch_channelise(const void *hist, long n_hist, const void *samples
     if (chan_ws_supported(dt, C, P, N, samples, n_samples)) {
         // spectra whose windows reach into the history and that the
         // warp-specialised kernel does not read itself: generic kernel
-        const long m_head = std::min(chan_ws_begin(dt, out_kind, N, t_stride, out, hist, n_hist), round_up(T, 64));
+        const long m_head = std::min(chan_ws_begin(dt, out_kind, N, t_stride, out, out_lo, hist, n_hist), round_up(T, 64));
         cudaError_t e = cudaSuccess;
         if (m_head > 0)
             e = launch_channelise_head(hist, n_hist, samples, n_samples, dt, n_sb, N, C, P, h, bandpass, tw, out_kind,

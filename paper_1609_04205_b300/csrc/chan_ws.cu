@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_ppf64_ws(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core variant for fp16 output.  The 64-point DFT of one (input,
+// Tensor-core variant for fp16 and split-fp16 output.  The 64-point DFT of one (input,
 // spectrum) is a product with the 64 x 64 complex DFT matrix.  In real form a
 // batch (eight inputs x 16 spectra) is one tcgen05.mma of M = 128, N = 128,
 // K = 128 (eight K = 16 steps), fp16 operands, fp32 accumulation in TMEM:
@@ -513,6 +513,19 @@ __global__ void __launch_bounds__(kThreadsWs, 1) k_ppf64_ws(const __grid_constan
 // spectrum that received its last tap leaves the ring.  Each spectrum still
 // sums h[0] x[s] + h[1] x[s+1] + ... in tap order, so its value equals the
 // direct form's.
+// Split-fp16 output (SPLIT: the hi and lo operand planes of the FP16x3 mode,
+// Sec. 4.2.5) keeps about fp32 accuracy through the transform: the FIR
+// outputs and the DFT matrix are each split into fp16 hi and lo parts, and
+// three MMAs per K step sum Yl Wh, Yh Wl and then Yh Wh into the fp32
+// accumulator (the small products first, so the accumulator's truncating
+// adds act on small partial sums; Yl Wl, about 2^-22 of the result, is
+// dropped).  The epilogue splits the scaled result into the hi and lo
+// planes.  The taps are scaled by 64 (exact) so that the lo parts of small
+// int8 samples stay clear of fp16's subnormal range; the bandpass weight
+// carries the 1/64.  The doubled operands leave int16 input one FIR operand
+// buffer (the FIR writes a batch once the MMAs have read the previous one)
+// and three input stages, int8 two of each.  A form with both DFT matrices
+// in tensor memory (the MMA's A operand) was slower and not deterministic.
 // Roles: warp 0 lane 0 TMA producer (input ring as in k_ppf64_ws, items of
 // eight inputs), warp 1 TMEM owner and MMA issuer, warps 2-5 epilogue (TMEM
 // lane quadrant = warp % 4), warps 6-13 FIR (thread = phase n, input pair).
@@ -524,19 +537,27 @@ constexpr uint32_t kTcCols = 512;        // four 128-column fp32 accumulators
 constexpr int kTcAcc = 4;
 constexpr uint32_t kTcIdesc = tc::idesc_f16_kmajor(128, 128);
 
-template <typename IN>
+constexpr float kTcTapScale = 64.f;      // split output: tap scale, undone in the epilogue
+
+// SPLIT (split-fp16 output): the DFT matrix and the FIR operand each have hi
+// and lo halves (32 KB apiece).  ci16 then keeps one FIR operand buffer and
+// three input stages, ci8 two buffers and two stages.
+template <typename IN, bool SPLIT = false>
 struct TcGeo {
     static constexpr int E = sizeof(IN);
     static constexpr int ROWB = kTcNI * E;                 // stage row: 32 B (ci16) or 16 B (ci8)
     static constexpr int STAGE = kRowsPerStage * ROWB;
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = !SPLIT ? 4 : (E == 4 ? 3 : 2);
+    static constexpr int NYB = !SPLIT || E != 4 ? 2 : 1;   // FIR operand buffers
+    static constexpr int WB = SPLIT ? 65536 : 32768;       // DFT matrix: hi, then lo 32 KB on (split)
+    static constexpr int YB = SPLIT ? 65536 : 32768;       // one FIR operand buffer: hi, then lo
     static constexpr int OFF_W = 0;                        // DFT matrix, 2 x [128 rows][128 B] SW128
-    static constexpr int OFF_Y = 32768;                    // FIR-output operands, two of 32 KB
-    static constexpr int OFF_X = OFF_Y + 65536;            // input ring
+    static constexpr int OFF_Y = WB;                       // FIR-output operands
+    static constexpr int OFF_X = OFF_Y + NYB * YB;         // input ring
     static constexpr int OFF_BAR = OFF_X + STAGES * STAGE;
     static constexpr int NBAR = 2 * STAGES + 4 + 2 * kTcAcc + 1;
     static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 1024;   // + alignment slack
-    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(SMEM + 1040 <= 227 * 1024, "shared memory (dynamic + the kernel's static arrays)");
 };
 
 __device__ __forceinline__ void unpack_pair(const unsigned char *p, float2 (&x)[2], short2) {
@@ -566,7 +587,7 @@ __device__ __forceinline__ void hist_pair(const void *h, long e, float2 (&x)[2],
 }
 
 // h0 >= 0: the batch's first sample lies in the history, at element h0.
-template <typename IN, bool MASK>
+template <typename IN, bool MASK, bool SPLIT>
 __device__ __forceinline__ void fir_batch_tc(const float2 (&hr)[kP], float2 (&acc)[2][kP], const unsigned char *xs,
                                              unsigned char *yb, int xoff, const int (&yx)[8], long m0, long T,
                                              const void *hist, long h0)
@@ -595,7 +616,13 @@ __device__ __forceinline__ void fir_batch_tc(const float2 (&hr)[kP], float2 (&ac
         for (int u = 0; u < 2; ++u) {
             float2 y = acc[u][mm & 15];
             if (MASK && m0 + mm >= T) y = make_float2(0.f, 0.f);
-            *reinterpret_cast<__half2 *>(yb + 128 * (16 * u + 8 * (mm & 1)) + yx[mm >> 1]) = __floats2half2_rn(y.x, y.y);
+            const int off = 128 * (16 * u + 8 * (mm & 1)) + yx[mm >> 1];
+            const __half2 hv = __floats2half2_rn(y.x, y.y);
+            *reinterpret_cast<__half2 *>(yb + off) = hv;
+            if constexpr (SPLIT) {
+                const float2 hf = __half22float2(hv);
+                *reinterpret_cast<__half2 *>(yb + 32768 + off) = __floats2half2_rn(y.x - hf.x, y.y - hf.y);
+            }
         }
     }
 }
@@ -606,9 +633,9 @@ __device__ __forceinline__ void fir_batch_tc(const float2 (&hr)[kP], float2 (&ac
 // store the (mm, mm + 1) pairs of the real and imaginary rows; the NB stores
 // of one row go out back to back (16 NB spectra of the row).  o: real row of
 // (channel t4, input 2q) at the window's first spectrum + mm.
-template <int NB>
-__device__ __forceinline__ void epi_window(uint32_t taddr, long g, __half *o, long cstride, long ts, const float2 *gs,
-                                           int t4)
+template <int NB, bool SPLIT>
+__device__ __forceinline__ void epi_window(uint32_t taddr, long g, __half *o, __half *olo, long cstride, long ts,
+                                           const float2 *gs, int t4)
 {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -624,27 +651,38 @@ __device__ __forceinline__ void epi_window(uint32_t taddr, long g, __half *o, lo
             for (int jj = 0; jj < 2; ++jj) {
                 const int c = t4 + 4 * (2 * j8 + jj);
                 const float2 gc = gs[c];
-                __half *orow = o + (long)(c - t4) * cstride + 2L * u * ts;
+                const long roff = (long)(c - t4) * cstride + 2L * u * ts;
+                __half *orow = o + roff;
 #pragma unroll
                 for (int k = 0; k < NB; ++k) {
                     const float2 re = __fmul2_rn(make_float2(__uint_as_float(r[k][4 * jj]), __uint_as_float(r[k][4 * jj + 2])), gc);
-                    *reinterpret_cast<__half2 *>(orow + kMB * k) = __floats2half2_rn(re.x, re.y);
+                    const __half2 h = __floats2half2_rn(re.x, re.y);
+                    *reinterpret_cast<__half2 *>(orow + kMB * k) = h;
+                    if constexpr (SPLIT) {
+                        const float2 hf = __half22float2(h);
+                        *reinterpret_cast<__half2 *>(olo + roff + kMB * k) = __floats2half2_rn(re.x - hf.x, re.y - hf.y);
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < NB; ++k) {
                     const float2 im = __fmul2_rn(make_float2(__uint_as_float(r[k][4 * jj + 1]), __uint_as_float(r[k][4 * jj + 3])), gc);
-                    *reinterpret_cast<__half2 *>(orow + ts + kMB * k) = __floats2half2_rn(im.x, im.y);
+                    const __half2 h = __floats2half2_rn(im.x, im.y);
+                    *reinterpret_cast<__half2 *>(orow + ts + kMB * k) = h;
+                    if constexpr (SPLIT) {
+                        const float2 hf = __half22float2(h);
+                        *reinterpret_cast<__half2 *>(olo + roff + ts + kMB * k) = __floats2half2_rn(im.x - hf.x, im.y - hf.y);
+                    }
                 }
             }
         }
     }
 }
 
-template <typename IN>
+template <typename IN, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constant__ WsParams P)
 {
-    using G = TcGeo<IN>;
-    constexpr int NS = G::STAGES;
+    using G = TcGeo<IN, SPLIT>;
+    constexpr int NS = G::STAGES, NYB = G::NYB;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ int abort_flag;
@@ -685,17 +723,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
         double sn, cs;
         sincospi((double)tid / 32.0, &sn, &cs);
         tw[tid] = make_float2((float)cs, (float)sn);
-        const float g = __ldg(P.bp + tid) * P.osc;
+        const float g = __ldg(P.bp + tid) * P.osc / (SPLIT ? kTcTapScale : 1.f);
         gs[tid] = make_float2(g, g);
     }
     __syncthreads();
-    // W row l = 2c + o, column pair (2n, 2n + 1): o = 0 (wr, -wi) = (cos, sin), o = 1 (wi, wr) = (-sin, cos)
+    // W row l = 2c + o, column pair (2n, 2n + 1): o = 0 (wr, -wi) = (cos, sin), o = 1 (wi, wr) = (-sin, cos);
+    // split output also stores lo = fp16(w - hi) 32 KB on
     for (int e = tid; e < 128 * kC; e += kTcThreads) {
         const int l = e >> 6, n = e & 63, c = l >> 1;
         const float2 t = tw[(n * c) & 63];
-        const __half2 v = (l & 1) == 0 ? __floats2half2_rn(t.x, t.y) : __floats2half2_rn(-t.y, t.x);
+        const float2 w = (l & 1) == 0 ? t : make_float2(-t.y, t.x);
+        const __half2 v = __floats2half2_rn(w.x, w.y);
         const int off = (n >> 5) * 16384 + l * 128 + ((((n & 31) >> 2) ^ (l & 7)) << 4) + 4 * (n & 3);
         *reinterpret_cast<__half2 *>(smem + G::OFF_W + off) = v;
+        if constexpr (SPLIT) {
+            const float2 vf = __half22float2(v);
+            *reinterpret_cast<__half2 *>(smem + G::OFF_W + 32768 + off) = __floats2half2_rn(w.x - vf.x, w.y - vf.y);
+        }
     }
     tc::fence_proxy_async();
     tc::fence_before();
@@ -743,18 +787,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
             for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
                 const ItemPos d = decode_item(P, item);
                 for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++g) {
-                    const int b = (int)(g & 1), da = (int)(g & (kTcAcc - 1));
-                    ok = bar_wait(yfull(b), (uint32_t)((g >> 1) & 1), &abort_flag, P.err, 32);
+                    // FIR operand buffer and its round (NYB is 1 or 2)
+                    const int b = NYB == 2 ? (int)(g & 1) : 0, da = (int)(g & (kTcAcc - 1));
+                    const long yr = NYB == 2 ? (g >> 1) : g;
+                    ok = bar_wait(yfull(b), (uint32_t)(yr & 1), &abort_flag, P.err, 32);
                     if (ok && g >= kTcAcc)
                         ok = bar_wait(dempty(da), (uint32_t)(((g / kTcAcc) - 1) & 1), &abort_flag, P.err, 33);
                     if (!ok) break;
                     tc::fence_after();
-                    const uint32_t ya = s0 + G::OFF_Y + b * 32768;
+                    const uint32_t ya = s0 + G::OFF_Y + b * G::YB, wa = s0 + G::OFF_W;
+                    if constexpr (SPLIT) {
+                        // Yl Wh and Yh Wl first (small partial sums for the
+                        // accumulator's truncating adds), then Yh Wh
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            const uint32_t koff = (ks >> 2) * 16384 + (ks & 3) * 32;
+                            tc::mma_f16(tmem + da * 128, tc::desc_kmajor_sw128(ya + 32768 + koff),
+                                        tc::desc_kmajor_sw128(wa + koff), kTcIdesc, ks > 0 ? 1u : 0u);
+                        }
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            const uint32_t koff = (ks >> 2) * 16384 + (ks & 3) * 32;
+                            tc::mma_f16(tmem + da * 128, tc::desc_kmajor_sw128(ya + koff),
+                                        tc::desc_kmajor_sw128(wa + 32768 + koff), kTcIdesc, 1u);
+                        }
+                    }
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks) {
                         const uint32_t koff = (ks >> 2) * 16384 + (ks & 3) * 32;
-                        tc::mma_f16(tmem + da * 128, tc::desc_kmajor_sw128(ya + koff),
-                                    tc::desc_kmajor_sw128(s0 + G::OFF_W + koff), kTcIdesc, ks > 0 ? 1u : 0u);
+                        tc::mma_f16(tmem + da * 128, tc::desc_kmajor_sw128(ya + koff), tc::desc_kmajor_sw128(wa + koff),
+                                    kTcIdesc, (SPLIT || ks > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(yempty(b));
                     tc::mma_commit(dfull(da));
@@ -776,12 +838,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
         const long cstride = 2L * P.N * P.t_stride;           // elements between channels
         __half *out = static_cast<__half *>(P.out);
+        __half *out_lo = static_cast<__half *>(P.out_lo);
         long g = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < P.n_items && ok; item += gridDim.x) {
             const ItemPos d = decode_item(P, item);
             // real row of (channel t4, input 2q), time mm
-            __half *ob = out + ((long)d.sb * kC * 2 * P.N + 2L * (d.grp * kTcNI + 2 * q)) * P.t_stride + t4 * cstride + mm;
+            const long obo = ((long)d.sb * kC * 2 * P.N + 2L * (d.grp * kTcNI + 2 * q)) * P.t_stride + t4 * cstride + mm;
+            __half *ob = out + obo;
+            __half *obl = SPLIT ? out_lo + obo : nullptr;
             for (long m0 = d.m_lo; m0 < d.m_hi && ok;) {
                 const long wend = min(d.m_hi, (m0 / (kTcAcc * kMB) + 1) * (kTcAcc * kMB));
                 const int nbw = (int)((wend - m0) / kMB);
@@ -790,11 +855,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
                                   P.err, 34);
                 if (!ok) break;
                 tc::fence_after();
+                __half *wl = SPLIT ? obl + m0 : nullptr;
                 switch (nbw) {
-                case 1: epi_window<1>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
-                case 2: epi_window<2>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
-                case 3: epi_window<3>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
-                default: epi_window<4>(taddr, g, ob + m0, cstride, P.t_stride, gs, t4); break;
+                case 1: epi_window<1, SPLIT>(taddr, g, ob + m0, wl, cstride, P.t_stride, gs, t4); break;
+                case 2: epi_window<2, SPLIT>(taddr, g, ob + m0, wl, cstride, P.t_stride, gs, t4); break;
+                case 3: epi_window<3, SPLIT>(taddr, g, ob + m0, wl, cstride, P.t_stride, gs, t4); break;
+                default: epi_window<4, SPLIT>(taddr, g, ob + m0, wl, cstride, P.t_stride, gs, t4); break;
                 }
                 tc::fence_before();
                 for (int k = 0; k < nbw; ++k) bar_arrive(dempty((int)((g + k) & (kTcAcc - 1))));
@@ -808,7 +874,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
         float2 hr[kP];
 #pragma unroll
         for (int k = 0; k < kP; ++k) {
-            const float hv = __ldg(P.h + k * kC + n);
+            const float hv = __ldg(P.h + k * kC + n) * (SPLIT ? kTcTapScale : 1.f);
             hr[k] = make_float2(hv, hv);
         }
         float2 acc[2][kP];
@@ -851,17 +917,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
                 ++L;
             }
             for (long m0 = d.m_lo; m0 < d.m_hi; m0 += kMB, ++g) {
-                const int b = (int)(g & 1);
-                if (g >= 2) ok = bar_wait(yempty(b), (uint32_t)(((g >> 1) - 1) & 1), &abort_flag, P.err, 36);
+                const int b = NYB == 2 ? (int)(g & 1) : 0;
+                const long yr = NYB == 2 ? (g >> 1) : g;
+                if (g >= NYB) ok = bar_wait(yempty(b), (uint32_t)((yr - 1) & 1), &abort_flag, P.err, 36);
                 if (ok) ok = bar_wait(xfull((int)(L % NS)), (uint32_t)((L / NS) & 1), &abort_flag, P.err, 37);
                 if (!ok) break;
                 const unsigned char *xs = smem + G::OFF_X + (L % NS) * G::STAGE;
-                unsigned char *yb = smem + G::OFF_Y + b * 32768;
+                unsigned char *yb = smem + G::OFF_Y + b * G::YB;
                 // the first batch's first sample is stream row 15 * 64 + n
                 const long r0 = (long)(kP - 1) * kC + n;
                 const long h0 = (from_hist && m0 == 0 && r0 < P.n_hist) ? hrow0 + r0 * P.N : -1;
-                if (m0 + kMB <= P.T) fir_batch_tc<IN, false>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
-                else fir_batch_tc<IN, true>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
+                if (m0 + kMB <= P.T) fir_batch_tc<IN, false, SPLIT>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
+                else fir_batch_tc<IN, true, SPLIT>(hr, acc, xs, yb, xoff, yx, m0, P.T, P.hist, h0);
                 tc::fence_proxy_async();
                 bar_arrive(xempty((int)(L % NS)));
                 bar_arrive(yfull(b));
@@ -878,11 +945,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ppf64_tc(const __grid_constan
     }
 }
 
-template <typename IN>
+template <typename IN, bool SPLIT>
 cudaError_t launch_tc_t(WsParams &P, int grid, cudaStream_t s)
 {
-    using G = TcGeo<IN>;
-    auto kern = k_ppf64_tc<IN>;
+    using G = TcGeo<IN, SPLIT>;
+    auto kern = k_ppf64_tc<IN, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
     // a block's warps spread over the SM's four register-file partitions:
@@ -917,10 +984,12 @@ bool chan_ws_supported(acf_in_dtype dt, int C, int P, int N, const void *samples
     return N % ni == 0 && reinterpret_cast<uintptr_t>(samples) % 16 == 0 && tensor_map_encoder() != nullptr;
 }
 
-// fp16 output takes the tensor-core DFT (items of eight inputs)
-static bool tc_variant(acf_in_dtype, int out_kind, int N, long t_stride, const void *out)
+// fp16 and split fp16 output take the tensor-core DFT (items of eight inputs)
+static bool tc_variant(acf_in_dtype, int out_kind, int N, long t_stride, const void *out, const void *out_lo)
 {
-    return out_kind == OUT_F16 && N % kTcNI == 0 && t_stride % 2 == 0 && reinterpret_cast<uintptr_t>(out) % 4 == 0;
+    auto a4 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 4 == 0; };
+    if (N % kTcNI != 0 || t_stride % 2 != 0 || !a4(out)) return false;
+    return out_kind == OUT_F16 || (out_kind == OUT_F16X3 && out_lo && a4(out_lo));
 }
 // ... which also covers the spectra whose windows reach into a history
 // shorter than one window (the streaming context's filter state)
@@ -936,9 +1005,11 @@ long chan_ws_first_spectrum(long n_hist)
     return round_up((n_hist + kC - 1) / kC, kMB);
 }
 
-long chan_ws_begin(acf_in_dtype dt, int out_kind, int N, long t_stride, const void *out, const void *hist, long n_hist)
+long chan_ws_begin(acf_in_dtype dt, int out_kind, int N, long t_stride, const void *out, const void *out_lo,
+                   const void *hist, long n_hist)
 {
-    if (tc_variant(dt, out_kind, N, t_stride, out) && (n_hist == 0 || tc_reads_history(dt, hist, n_hist))) return 0;
+    if (tc_variant(dt, out_kind, N, t_stride, out, out_lo) && (n_hist == 0 || tc_reads_history(dt, hist, n_hist)))
+        return 0;
     return chan_ws_first_spectrum(n_hist);
 }
 
@@ -946,7 +1017,7 @@ cudaError_t launch_chan_ws(const void *hist, const void *samples, long n_samples
                            int n_sb, int N, const float *h, const float *bp, float scale, int out_kind, void *out,
                            void *out_lo, long t_stride, long T, cudaStream_t s)
 {
-    const long m_begin = chan_ws_begin(dt, out_kind, N, t_stride, out, hist, n_hist);
+    const long m_begin = chan_ws_begin(dt, out_kind, N, t_stride, out, out_lo, hist, n_hist);
     const long m_end = round_up(T, 64);
     if (m_end <= m_begin) return cudaSuccess;
     const int E = in_elem_bytes(dt);
@@ -954,7 +1025,7 @@ cudaError_t launch_chan_ws(const void *hist, const void *samples, long n_samples
     if (!enc) return cudaErrorNotSupported;
     WsParams P;
     std::memset(&P, 0, sizeof(P));
-    const bool use_tc = tc_variant(dt, out_kind, N, t_stride, out);
+    const bool use_tc = tc_variant(dt, out_kind, N, t_stride, out, out_lo);
     if (use_tc && m_begin == 0 && n_hist > 0) {
         P.hist = hist;
         P.n_hist = n_hist;
@@ -1008,7 +1079,9 @@ cudaError_t launch_chan_ws(const void *hist, const void *samples, long n_samples
     if (items > 0x7fffffffL) return cudaErrorInvalidValue;
     P.n_items = (int)items;
     const int grid = (int)std::min<long>(items, sms);
-    if (use_tc) return dt == ACF_IN_CI16 ? launch_tc_t<short2>(P, grid, s) : launch_tc_t<char2>(P, grid, s);
+    if (use_tc && out_kind == OUT_F16X3)
+        return dt == ACF_IN_CI16 ? launch_tc_t<short2, true>(P, grid, s) : launch_tc_t<char2, true>(P, grid, s);
+    if (use_tc) return dt == ACF_IN_CI16 ? launch_tc_t<short2, false>(P, grid, s) : launch_tc_t<char2, false>(P, grid, s);
     if (dt == ACF_IN_CI16) {
         switch (out_kind) {
         case OUT_F32: return launch_ws_t<short2, OUT_F32>(P, grid, s);

@@ -197,6 +197,38 @@ def test_correlator_streaming_pushes_ci16(C):
             assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
 
 
+@pytest.mark.parametrize("dtype,N", [("ci16", 48), ("ci8", 64)])
+def test_correlator_streaming_split_tensor_core_channeliser(dtype, N):
+    """64-channel split-FP16 context with an input count divisible by eight:
+    every push goes through the tensor-core channeliser's split form (hi/lo
+    FIR operands and DFT matrix, three MMAs per K step; one operand buffer
+    and three input stages for int16, two and two for int8), which reads the
+    filter history itself.  Ragged pushes, integrations of two pushes,
+    against the oracle's stream partition at the FP32 tolerance."""
+    _dev()
+    P, C = 16, 64
+    pushes = [5000, 1300, 64 * 40 + 7, 260, 9000]
+    S = sum(pushes)
+    sky = synth.make_sky(N, 2, (0.1, 0.4), 79)
+    x = synth.voltages(N, S, 2, dtype, 512.0 if dtype == "ci16" else 16.0, sky, 79, device="cuda")
+    xs = x.cpu().numpy()
+    with acf.Correlator(N, 2, C, P, 2, "fp16x3", dtype, max(pushes)) as c:
+        outs = []
+        t0 = 0
+        for n in pushes:
+            c.push(x[:, t0:t0 + n].contiguous())
+            t0 += n
+            V = c.visibilities()
+            if V is not None:
+                outs.append(V.clone())
+        assert len(outs) == 2
+    torch.cuda.synchronize()
+    for sb in range(2):
+        ref = oracle.correlator(xs[sb], P, C, push_sizes=pushes, n_integrate=2)
+        for k in range(2):
+            assert norm_err(_np_complex(outs[k][sb]), ref[k], N) <= TOL_FP32
+
+
 @pytest.mark.parametrize("N", [70, 33])
 def test_correlator_streaming_256ch_ci8_corner_turn(N):
     """256-channel context on complex int8 over ragged pushes: each push is
