@@ -42,7 +42,7 @@ __device__ __forceinline__ double df_value(float sh, float sl) { return (double)
 // Exact-in-effect tests of |v|^2 > t: the fp32 square pf = fma(x, x, y*y)
 // (relative error below 2^-23) is compared with a threshold tf that carries a
 // relative error of at most 2^-22, widened by a 2^-20 guard band on either
-// side; outside the band the fp32 verdict equals the exact one, inside it the
+// side; outside the band the fp32 decision equals the exact one, inside it the
 // caller settles the element with the fp64 square (exact for fp32 inputs up
 // to the final rounding) against the fp64 threshold.  The fp64 work stays out
 // of the per-element loops (band hits are collected in bit masks and settled
