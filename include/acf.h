@@ -408,9 +408,10 @@ acf_status acf_batch_query_plan(const acf_batch *b, int *pair, int *order);
 
 /* Choose the plan instead of the autotuner: pair 0 or 1 (pair = 1 needs
  * n_tile 256), n_tile 128 or 256, k_split 1, 2 or 4, order 0, 1 or 2 (as
- * acf_batch_query_plan reports them).  The next acf_batch_run rebuilds the
- * work list and re-captures its graph.  ACF_EINVAL for other values (the
- * batch keeps its plan). */
+ * acf_batch_query_plan reports them).  The call first waits until the device
+ * is idle (a replay of the batch's graph may still run), then drops the
+ * graph; the next acf_batch_run rebuilds the work list and re-captures it.
+ * ACF_EINVAL for other values (the batch keeps its plan). */
 acf_status acf_batch_set_plan(acf_batch *b, int pair, int n_tile, int k_split, int order);
 acf_status acf_batch_destroy(acf_batch *b);
 const char *acf_batch_last_error(const acf_batch *b);
