@@ -352,9 +352,9 @@ acf_status acf_gain_backward(const void *R, const void *V, const void *g, int n_
  *   - The per-block loss partials live in a fixed device array inside the
  *     library of 65,536 floats (256 KiB), held by every GPU that loads the
  *     library until the process exits.  Problems needing more partials than
- *     that -- m (m + 1) / 2 * 4 * ceil(n_channels / 4) > 65,536 with
- *     m = ceil(n_inputs / 64), counted in 64 bits (for a multiple of 4
- *     channels: m (m + 1) / 2 * n_channels) -- are rejected with ACF_EINVAL
+ *     that -- m (m + 1) / 2 * 4 * ceil(n_channels / 8) > 65,536 with
+ *     m = ceil(n_inputs / 64), counted in 64 bits (for a multiple of 8
+ *     channels: m (m + 1) / 2 * n_channels / 2) -- are rejected with ACF_EINVAL
  *     before anything is enqueued; acf_gain_forward handles them.
  *   - The first call on a device looks up the array's device address (no
  *     allocation) and keeps it.  cudaDeviceReset unloads the library's

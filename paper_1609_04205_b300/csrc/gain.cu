@@ -14,7 +14,7 @@
 // them and multiplies by g once: per element and channel that leaves w R,
 // the residual, |E|^2 and z.
 //
-// A block owns a 16-row x 64-column tile for KCH = 4 consecutive channels
+// A block owns a 16-row x 64-column tile for KCH = 8 consecutive channels
 // (lane: two columns; warp: two rows), computes w_ij once, keeps the loads of
 // two channels in flight ahead of the arithmetic, then reduces: row sums by
 // a warp butterfly over the four (row, re/im) values, column sums across the
@@ -30,7 +30,7 @@
 namespace acf {
 namespace {
 
-constexpr int KCH = 4;            // channels per block
+constexpr int KCH = 8;            // channels per block
 constexpr int TR = 16, TC = 64;   // tile rows, columns
 
 // Programmatic dependent launch: a kernel launched with the programmatic
@@ -56,7 +56,7 @@ __device__ __forceinline__ void tile_decode(int k, int &rb, int &cb) {
     cb = rem % (sr + 1);
 }
 
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
 k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 *__restrict__ g,
        int N, int C, float *__restrict__ partials, float2 *__restrict__ grad)
 {
@@ -114,16 +114,15 @@ k_gain(const float2 *__restrict__ R, const float2 *__restrict__ V, const float2 
                 zacc[a][b].y += z.y;
             }
     };
-    // two channels in flight ahead of the arithmetic
-    float2 r0[2][2], v0[2][2], r1[2][2], v1[2][2], r2[2][2], v2[2][2];
-    load(r0, v0, 0);
-    load(r1, v1, 1);
-    load(r2, v2, 2);
-    accumulate(r0, v0);
-    load(r0, v0, 3);
-    accumulate(r1, v1);
-    accumulate(r2, v2);
-    accumulate(r0, v0);
+    // two channels in flight ahead of the arithmetic (three rotating buffers)
+    float2 rbuf[3][2][2], vbuf[3][2][2];
+#pragma unroll
+    for (int k = 0; k < 3 && k < KCH; ++k) load(rbuf[k], vbuf[k], k);
+#pragma unroll
+    for (int cc = 0; cc < KCH; ++cc) {
+        accumulate(rbuf[cc % 3], vbuf[cc % 3]);
+        if (cc + 3 < KCH) load(rbuf[cc % 3], vbuf[cc % 3], cc + 3);
+    }
 
     // grad was zeroed by the kernel before this one, which may still be running
     dep_wait();

@@ -91,7 +91,7 @@ def test_library_prototype_matches_oracle(P, C):
 
 @pytest.mark.parametrize("entry", ["acf_gain_forward_noalloc", "acf_gain_forward"])
 def test_gain_rejects_sizes_whose_partial_count_overflows_32_bits(entry):
-    """2,900,000 inputs over 3 channels need m(m+1)/2 * 4 * ceil(3/4) = 4.1e9
+    """2,900,000 inputs over 3 channels need m(m+1)/2 * 4 * ceil(3/8) = 4.1e9
     loss partials (m = ceil(N/64)), past 2^31: the count is kept in 64 bits, so the
     allocation-free entry point rejects it on the host (its fixed scratch holds
     65,536) and the allocating one rejects a channel count past the grid's
